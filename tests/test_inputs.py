@@ -1,0 +1,47 @@
+"""The seeded workload generators: reproducible, non-overlapping, the stated shapes."""
+import math
+
+import numpy as np
+
+from paper_2310_12651_gb300 import inputs
+
+
+def _min_periodic_distance(Y, L):
+    d = Y[:, None, :] - Y[None, :, :]
+    d -= L * np.round(d / L)
+    r = np.sqrt(np.einsum("ijk,ijk->ij", d, d))
+    np.fill_diagonal(r, np.inf)
+    return r.min()
+
+
+def test_box_edge_matches_volume_fraction():
+    L = inputs.box_edge(65536, 0.05)
+    assert abs(L - 176.41391792668995) < 1e-9
+    assert abs(65536 * 4 * math.pi / 3 / L ** 3 - 0.05) < 1e-15
+
+
+def test_random_suspension_is_reproducible_and_non_overlapping():
+    L = inputs.box_edge(800, 0.1)
+    a = inputs.random_suspension(800, L, 5)
+    b = inputs.random_suspension(800, L, 5)
+    assert np.array_equal(a, b)
+    assert a.shape == (800, 3) and np.all(a >= 0) and np.all(a < L)
+    assert _min_periodic_distance(a, L) >= 2.2
+
+
+def test_random_loads_are_mean_free():
+    F, T = inputs.random_loads(1000, 9)
+    assert np.max(np.abs(F.mean(axis=0))) < 1e-15 and np.max(np.abs(T.mean(axis=0))) < 1e-15
+    F2, T2 = inputs.random_loads(1000, 9, torques=False, bias=(0, 0, -1))
+    assert T2 is None and abs(F2[:, 2].mean() + 1) < 1e-14
+
+
+def test_random_rods_geometry():
+    L = 60.0
+    Y, phi = inputs.random_rods(6, 8, L, 3)
+    assert Y.shape == (48, 3)
+    assert _min_periodic_distance(Y, L) >= 2.2 - 1e-9
+    # consecutive spheres of a rod sit one bond apart
+    d = Y[1:8] - Y[0:7]
+    d -= L * np.round(d / L)
+    np.testing.assert_allclose(np.linalg.norm(d, axis=1), 2.2, atol=1e-9)
