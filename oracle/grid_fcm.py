@@ -254,3 +254,44 @@ def fast_fcm_apply(Y, F, T, L, M, M_G, Sigma, R_c, Sigma_D=None, a=1.0, eta=1.0)
     Ug, Wg = grid_apply(Y, F, T, L, M, M_G, Sigma, Sigma_D, a, eta)
     Up, Wp = pair_correction(Y, F, T, L, R_c, Sigma, Sigma_D, a, eta)
     return Ug + Up, Wg + Wp
+
+
+def pair_correction_subset(Y, F, T, L, R_c, Sigma, Sigma_D, idx, a=1.0, eta=1.0):
+    """Rows ``idx`` of :func:`pair_correction`, each computed on its own from the
+    particles within R_c of it (used to check large systems on sampled particles)."""
+    L = _as3(L)
+    Yw = wrap(Y, L)
+    F = np.asarray(F, dtype=np.float64)
+    idx = np.asarray(idx, dtype=np.int64)
+    U = cf.self_correction_VF(Sigma, a, eta) * F[idx]
+    W = np.zeros((idx.size, 3))
+    if T is not None:
+        T = np.asarray(T, dtype=np.float64)
+        W = W + cf.self_correction_WT(Sigma_D, a, eta) * T[idx]
+    tree = cKDTree(Yw, boxsize=L)
+    for row, i in enumerate(idx):
+        nb = np.array(tree.query_ball_point(Yw[i], R_c), dtype=np.int64)
+        nb = nb[nb != i]
+        if nb.size == 0:
+            continue
+        x = Yw[i][None, :] - Yw[nb]
+        x = x - L * np.round(x / L)
+        r = np.linalg.norm(x, axis=1)
+        keep = r < R_c
+        nb, x, r = nb[keep], x[keep], r[keep]
+        if nb.size == 0:
+            continue
+        coincident = r == 0.0
+        xs_ = np.where(coincident[:, None], np.array([1.0, 0.0, 0.0]), x)
+        vf = cf.correction_VF(xs_, Sigma, a, eta)
+        vf[coincident] = cf.self_correction_VF(Sigma, a, eta) * np.eye(3)
+        U[row] += np.einsum("pab,pb->a", vf, F[nb])
+        if T is not None:
+            wf = cf.correction_WF(xs_, Sigma, Sigma_D, a, eta)
+            wf[coincident] = 0.0
+            wt = cf.correction_WT(xs_, Sigma, Sigma_D, a, eta)
+            wt[coincident] = cf.self_correction_WT(Sigma_D, a, eta) * np.eye(3)
+            vt = np.swapaxes(-wf, -1, -2)
+            U[row] += np.einsum("pab,pb->a", vt, T[nb])
+            W[row] += np.einsum("pab,pb->a", wf, F[nb]) + np.einsum("pab,pb->a", wt, T[nb])
+    return U, W

@@ -1,0 +1,151 @@
+// Spatial hashing, counting sort and cell lists (Section 4, steps 1-2).
+//
+// Two keys per particle: the spread/gather tile that holds the first point of
+// its M_G^3 window, and the pair cell of Section 4 step 1 (m_i = max(int(L_i/r_c), 3)
+// cells, index x_c + (y_c + z_c m_y) m_x). Counting sort by each key gives the
+// tile-sorted arrays used by spread/gather and the cell-sorted arrays with
+// start offsets used by the pair correction. The rank of a particle inside its
+// bin is the value its atomic increment returned, so three kernels suffice:
+// key+count, scan, scatter. The scan leaves the counters at zero for the next call.
+#include "fcm_internal.cuh"
+
+namespace fcm {
+
+template <typename R>
+__global__ void __launch_bounds__(256) key_count_kernel(Geometry<R> g, int n, const R* __restrict__ pos,
+                                                        BinBuffers b, int need_cells) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int bad = 0;
+  int t[3], c[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    R y = wrap_coord(pos[3 * (size_t)i + d], g.L[d], &bad);
+    int i0 = pmod(window_start(y, g.h[d], g.MG), g.M[d]);
+    t[d] = i0 / g.tile[d];
+    c[d] = cell_coord(y, g.cellw_inv[d], g.mcell[d]);
+  }
+  if (bad) atomicOr(b.status, kStatusNonFinite);
+  unsigned tk = (unsigned)(t[0] + g.ntile[0] * (t[1] + g.ntile[1] * t[2]));
+  b.tile_key[i] = tk;
+  b.tile_rank[i] = (unsigned)atomicAdd(&b.tile_count[tk], 1);
+  if (need_cells) {
+    unsigned ck = (unsigned)(c[0] + g.mcell[0] * (c[1] + g.mcell[1] * c[2]));
+    b.cell_key[i] = ck;
+    b.cell_rank[i] = (unsigned)atomicAdd(&b.cell_count[ck], 1);
+  }
+}
+
+// Exclusive scan of one counter array by one block; start[nb] = total. Resets counts.
+__device__ void block_scan(int* count, int* start, int nb) {
+  __shared__ int warp_sums[32];
+  __shared__ int carry;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int chunk = (nb + nthr - 1) / nthr;
+  const int lo = min(nb, tid * chunk), hi = min(nb, lo + chunk);
+  int local = 0;
+  for (int k = lo; k < hi; ++k) local += count[k];
+  // inclusive warp scan of the per-thread sums
+  int lane = tid & 31, wid = tid >> 5;
+  int v = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += u;
+  }
+  if (lane == 31) warp_sums[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    int nw = (nthr + 31) / 32;
+    int w = lane < nw ? warp_sums[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int u = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += u;
+    }
+    if (lane < nw) warp_sums[lane] = w;
+    if (lane == nw - 1) carry = w;
+  }
+  __syncthreads();
+  int excl = v - local + (wid > 0 ? warp_sums[wid - 1] : 0);
+  for (int k = lo; k < hi; ++k) {
+    int cnt = count[k];
+    start[k] = excl;
+    excl += cnt;
+    count[k] = 0;
+  }
+  if (tid == 0) start[nb] = carry;
+}
+
+__global__ void __launch_bounds__(1024) scan_kernel(BinBuffers b, int need_cells) {
+  if (blockIdx.x == 0) block_scan(b.tile_count, b.tile_start, b.ntiles);
+  else if (need_cells) block_scan(b.cell_count, b.cell_start, b.ncells);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) scatter_kernel(Geometry<R> g, int n, const R* __restrict__ pos,
+                                                      const R* __restrict__ F, const R* __restrict__ T,
+                                                      BinBuffers b, int need_cells) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int bad = 0;
+  Vec4<R> p, f, t;
+  p.x = wrap_coord(pos[3 * (size_t)i + 0], g.L[0], &bad);
+  p.y = wrap_coord(pos[3 * (size_t)i + 1], g.L[1], &bad);
+  p.z = wrap_coord(pos[3 * (size_t)i + 2], g.L[2], &bad);
+  p.w = as_real_bits(i, R(0));
+  f.x = F[3 * (size_t)i + 0]; f.y = F[3 * (size_t)i + 1]; f.z = F[3 * (size_t)i + 2]; f.w = R(0);
+  if (T) { t.x = T[3 * (size_t)i + 0]; t.y = T[3 * (size_t)i + 1]; t.z = T[3 * (size_t)i + 2]; }
+  else   { t.x = R(0); t.y = R(0); t.z = R(0); }
+  t.w = R(0);
+  // keys and ranks come from key_count_kernel; both bins are in range by construction
+  int dt = b.tile_start[b.tile_key[i]] + (int)b.tile_rank[i];
+  dt = min(max(dt, 0), n - 1);
+  ((Vec4<R>*)b.t_pos)[dt] = p;
+  ((Vec4<R>*)b.t_F)[dt] = f;
+  ((Vec4<R>*)b.t_T)[dt] = t;
+  if (need_cells) {
+    int dc = b.cell_start[b.cell_key[i]] + (int)b.cell_rank[i];
+    dc = min(max(dc, 0), n - 1);
+    ((Vec4<R>*)b.c_pos)[dc] = p;
+    ((Vec4<R>*)b.c_F)[dc] = f;
+    ((Vec4<R>*)b.c_T)[dc] = t;
+  }
+}
+
+template <typename R>
+void launch_binning(const Geometry<R>& g, int n, const R* pos, const R* F, const R* T,
+                    const BinBuffers& b, bool need_cells, cudaStream_t s, long long* launches) {
+  if (n <= 0) return;
+  int blocks = (n + 255) / 256;
+  key_count_kernel<R><<<blocks, 256, 0, s>>>(g, n, pos, b, need_cells ? 1 : 0);
+  scan_kernel<<<2, 1024, 0, s>>>(b, need_cells ? 1 : 0);
+  scatter_kernel<R><<<blocks, 256, 0, s>>>(g, n, pos, F, T, b, need_cells ? 1 : 0);
+  *launches += 3;
+}
+
+template void launch_binning<float>(const Geometry<float>&, int, const float*, const float*, const float*,
+                                    const BinBuffers&, bool, cudaStream_t, long long*);
+template void launch_binning<double>(const Geometry<double>&, int, const double*, const double*, const double*,
+                                     const BinBuffers&, bool, cudaStream_t, long long*);
+
+__global__ void zero_kernel(uint4* p, size_t n16, unsigned char* tail, size_t ntail) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t k = i; k < n16; k += stride) p[k] = make_uint4(0, 0, 0, 0);
+  if (i < ntail) tail[i] = 0;
+}
+
+void launch_zero(void* p, size_t bytes, cudaStream_t s, long long* launches) {
+  if (bytes == 0) return;
+  size_t n16 = bytes / 16, ntail = bytes - n16 * 16;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  size_t want = (n16 + 255) / 256;
+  int blocks = (int)(want < (size_t)sms * 8 ? (want > 0 ? want : 1) : (size_t)sms * 8);
+  zero_kernel<<<blocks, 256, 0, s>>>((uint4*)p, n16, (unsigned char*)p + n16 * 16, ntail);
+  *launches += 1;
+}
+
+}  // namespace fcm

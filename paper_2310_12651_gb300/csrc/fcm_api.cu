@@ -1,0 +1,675 @@
+// libfcm C-ABI: handle lifetime, parameter checks, workspace, and the launch
+// sequence of one mobility product (Section 4):
+//
+//   caller stream : bin ──► zero grid ─► spread ─► R2C ─► project ─► C2R ─┐
+//                     └─(event)─► side stream: pair correction ──(event)─┴► gather (+ pair sums) ─► U, W
+//
+// The pair correction only needs the cell-sorted particles, so it runs on the
+// handle's side stream while the grid stages run; the gather kernel adds the
+// pair sums when it writes U and W in input order. The fork/join uses events
+// only, so a caller may capture fcm_apply into a CUDA graph.
+#include <cufft.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/fcm.h"
+#include "fcm_internal.cuh"
+
+using namespace fcm;
+
+namespace {
+
+thread_local std::string g_error;
+
+int fail(int code, const std::string& msg) {
+  g_error = msg;
+  return code;
+}
+
+#define FCM_CUDA(call)                                                                       \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return fail(e_ == cudaErrorMemoryAllocation ? FCM_ERR_OOM : FCM_ERR_CUDA,              \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                       \
+  } while (0)
+
+#define FCM_CUFFT(call)                                                                      \
+  do {                                                                                       \
+    cufftResult r_ = (call);                                                                 \
+    if (r_ != CUFFT_SUCCESS) return fail(FCM_ERR_CUFFT, std::string(#call) + " failed: " +   \
+                                              std::to_string((int)r_));                      \
+  } while (0)
+
+struct StageEvents {
+  cudaEvent_t a, b;
+  int stage;
+};
+
+class DeviceGuard {
+ public:
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev_);
+    if (prev_ != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() { cudaSetDevice(prev_); }
+ private:
+  int prev_ = 0;
+};
+
+double gauss_moment(double s2, int m) {  // int_0^inf exp(-s2 k^2) k^(2m) dk
+  return std::tgamma(m + 0.5) / (2.0 * std::pow(s2, m + 0.5));
+}
+
+double factorial(int k) {
+  double f = 1.0;
+  for (int i = 2; i <= k; ++i) f *= i;
+  return f;
+}
+
+double double_factorial(int k) {
+  double f = 1.0;
+  for (int i = k; i > 1; i -= 2) f *= i;
+  return f;
+}
+
+}  // namespace
+
+namespace fcm {
+
+// Constants of pair_coeffs, and the Taylor coefficients of each radial
+// function: the correction blocks are Fourier integrals of radial kernels
+// (Appendix A for VF), so expanding exp(i k.x) in powers of k.x gives series in
+// r^2 whose coefficients are angular averages times Gaussian moments of the kernels.
+void make_pair_consts(double a, double eta, double Sigma, double Sigma_D, double r_c, double r_series,
+                      PairConsts<double>* o) {
+  const double pi = kPi;
+  const double sg = a / std::sqrt(pi);
+  const double sD = a / std::cbrt(6.0 * std::sqrt(pi));
+  std::memset(o, 0, sizeof(*o));
+  o->eta = eta;
+  o->sg2 = sg * sg;
+  o->Sg2 = Sigma * Sigma;
+  o->dd = sg * sg - Sigma * Sigma;
+  o->inv2sg = 1.0 / (2.0 * sg);
+  o->inv2Sg = 1.0 / (2.0 * Sigma);
+  o->nA = std::pow(4.0 * pi * sg * sg, -1.5);
+  o->eA = 1.0 / (4.0 * sg * sg);
+  o->nB = std::pow(4.0 * pi * Sigma * Sigma, -1.5);
+  o->eB = 1.0 / (4.0 * Sigma * Sigma);
+  o->sg4 = o->sg2 * o->sg2;
+  o->Sg4 = o->Sg2 * o->Sg2;
+  const double s1 = std::sqrt(sg * sg + sD * sD), s2 = std::sqrt(Sigma * Sigma + Sigma_D * Sigma_D);
+  o->k1 = 1.0 / (s1 * std::sqrt(2.0));
+  o->k2 = 1.0 / (s2 * std::sqrt(2.0));
+  o->s1sq = s1 * s1;
+  o->s2sq = s2 * s2;
+  o->n1 = std::pow(2.0 * pi * s1 * s1, -1.5);
+  o->e1 = 1.0 / (2.0 * s1 * s1);
+  o->n2 = std::pow(2.0 * pi * s2 * s2, -1.5);
+  o->e2 = 1.0 / (2.0 * s2 * s2);
+  o->inv2sD = 1.0 / (2.0 * sD);
+  o->inv2SD = 1.0 / (2.0 * Sigma_D);
+  o->sD2 = sD * sD;
+  o->SD2 = Sigma_D * Sigma_D;
+  o->nDa = std::pow(4.0 * pi * sD * sD, -1.5);
+  o->eDa = 1.0 / (4.0 * sD * sD);
+  o->nDb = std::pow(4.0 * pi * Sigma_D * Sigma_D, -1.5);
+  o->eDb = 1.0 / (4.0 * Sigma_D * Sigma_D);
+  const double dd = o->dd;
+  const double sp = Sigma * std::sqrt(pi);
+  o->selfVF = 1.0 / (6.0 * pi * eta * a) - 1.0 / (6.0 * pi * eta * sp) + dd / (12.0 * eta * sp * sp * sp) -
+              dd * dd / (32.0 * eta * std::pow(Sigma, 5) * std::pow(pi, 1.5));
+  const double spD = Sigma_D * std::sqrt(pi);
+  o->selfWT = 1.0 / (8.0 * pi * eta * a * a * a) - 1.0 / (48.0 * eta * spD * spD * spD);
+  o->rs2 = r_series * r_series;
+  o->rc2 = r_c * r_c;
+  // Taylor series
+  const double S2 = Sigma * Sigma, SD2 = Sigma_D * Sigma_D;
+  const double e1sq = 0.5 * (sg * sg + sD * sD), e2sq = 0.5 * (S2 + SD2);
+  auto mVF = [&](int j) {
+    return gauss_moment(sg * sg, j) - gauss_moment(S2, j) + dd * gauss_moment(S2, j + 1) -
+           0.25 * dd * dd * gauss_moment(S2, j + 2);
+  };
+  auto mWT = [&](int j) { return gauss_moment(sD * sD, j + 1) - gauss_moment(SD2, j + 1); };
+  auto mWF = [&](int j) {
+    return gauss_moment(e1sq, j + 1) - gauss_moment(e2sq, j + 1) + 0.5 * dd * gauss_moment(e2sq, j + 2);
+  };
+  for (int j = 0; j <= kSeriesTerms; ++j) {
+    const double sgn = (j % 2 == 0) ? 1.0 : -1.0;
+    const double ang = 1.0 / ((2.0 * j + 1.0) * (2.0 * j + 3.0));
+    const double base_vf = sgn * mVF(j) / (factorial(2 * j) * 2.0 * pi * pi * eta) * ang;
+    const double base_wt = sgn * mWT(j) / (factorial(2 * j) * 8.0 * pi * pi * eta) * ang;
+    if (j < kSeriesTerms) {
+      o->ser_al[j] = base_vf * (2.0 * j + 2.0);
+      o->ser_gm[j] = base_wt * (2.0 * j + 2.0);
+      o->ser_cr[j] = sgn * mWF(j) / (4.0 * pi * pi * eta * std::pow(2.0, j) * factorial(j) * double_factorial(2 * j + 3));
+    }
+    if (j >= 1) {
+      o->ser_bt[j - 1] = -base_vf * (2.0 * j);
+      o->ser_dl[j - 1] = -base_wt * (2.0 * j);
+    }
+  }
+}
+
+void narrow_pair_consts(const PairConsts<double>& in, PairConsts<float>* o) {
+  const double* src = reinterpret_cast<const double*>(&in);
+  float* dst = reinterpret_cast<float*>(o);
+  static_assert(sizeof(PairConsts<double>) == 2 * sizeof(PairConsts<float>), "layout");
+  for (size_t k = 0; k < sizeof(PairConsts<float>) / sizeof(float); ++k) dst[k] = (float)src[k];
+}
+
+}  // namespace fcm
+
+struct fcm_handle {
+  fcm_params p{};
+  int device = 0;
+  bool fp64 = false;
+  bool pairs_on = false;
+  Geometry<float> gf{};
+  Geometry<double> gd{};
+  KernelConsts<float> kf{};
+  KernelConsts<double> kd{};
+  PairConsts<float> pf{};
+  PairConsts<double> pd{};
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  BinBuffers bb{};
+  void* grid = nullptr;
+  void* spec = nullptr;
+  void* upair = nullptr;
+  void* wpair = nullptr;
+  void* wscratch = nullptr;
+  size_t grid_bytes = 0;
+  cufftHandle r2c = 0, c2r = 0;
+  bool plans = false;
+  size_t bytes = 0;
+  long long launches = 0;
+  std::vector<void*> allocs;
+  bool timing = false;
+  std::vector<StageEvents> pool;
+  std::vector<int> pending;
+  size_t next_event = 0;
+  double ms[FCM_NUM_STAGES] = {0};
+  long long counts[FCM_NUM_STAGES] = {0};
+};
+
+namespace {
+
+int halloc(fcm_handle* h, void** out, size_t bytes) {
+  bytes = (bytes + 255) / 256 * 256;
+  if (bytes == 0) bytes = 256;
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(FCM_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+  }
+  h->allocs.push_back(p);
+  h->bytes += bytes;
+  *out = p;
+  return FCM_OK;
+}
+
+void release(fcm_handle* h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  cudaDeviceSynchronize();
+  if (h->plans) {
+    cufftDestroy(h->r2c);
+    cufftDestroy(h->c2r);
+  }
+  for (auto& ev : h->pool) {
+    cudaEventDestroy(ev.a);
+    cudaEventDestroy(ev.b);
+  }
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->side) cudaStreamDestroy(h->side);
+  for (void* p : h->allocs) cudaFree(p);
+  delete h;
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0; }
+
+void choose_tile(const fcm_params& p, int tile[3]) {
+  if (p.tile[0] > 0 && p.tile[1] > 0 && p.tile[2] > 0) {
+    for (int d = 0; d < 3; ++d) tile[d] = std::min(p.tile[d], p.M[d]);
+    return;
+  }
+  static const int cands[][3] = {{8, 8, 8}, {8, 8, 4}, {8, 4, 4}, {4, 4, 4}, {4, 4, 2}, {4, 2, 2},
+                                 {2, 2, 2}, {2, 2, 1}, {2, 1, 1}, {1, 1, 1}};
+  const size_t budgets[2] = {113 * 1024, (size_t)tile_smem_limit()};
+  for (size_t budget : budgets) {
+    for (auto& c : cands) {
+      int t[3] = {std::min(c[0], p.M[0]), std::min(c[1], p.M[1]), std::min(c[2], p.M[2])};
+      if (tile_smem_bytes(t, p.M_G) <= budget) {
+        tile[0] = t[0]; tile[1] = t[1]; tile[2] = t[2];
+        return;
+      }
+    }
+  }
+  tile[0] = tile[1] = tile[2] = 1;
+}
+
+template <typename R>
+void fill_geometry(const fcm_params& p, const int tile[3], Geometry<R>* g) {
+  for (int d = 0; d < 3; ++d) {
+    g->L[d] = (R)p.L[d];
+    g->h[d] = (R)(p.L[d] / p.M[d]);
+    g->M[d] = p.M[d];
+    g->tile[d] = tile[d];
+    g->ntile[d] = (p.M[d] + tile[d] - 1) / tile[d];
+    int m = (p.r_c > 0) ? (int)(p.L[d] / p.r_c) : 3;
+    g->mcell[d] = std::max(m, 3);
+    g->cellw_inv[d] = (R)(g->mcell[d] / p.L[d]);
+  }
+  g->MG = p.M_G;
+}
+
+template <typename R>
+void fill_kernel_consts(const fcm_params& p, double SigmaD, KernelConsts<R>* k) {
+  const double pi = kPi;
+  const double sg = p.a / std::sqrt(pi);
+  const double S = p.Sigma, dd = sg * sg - S * S;
+  k->inv2S2 = (R)(1.0 / (2.0 * S * S));
+  k->inv2SD2 = (R)(1.0 / (2.0 * SigmaD * SigmaD));
+  k->nrm = (R)std::pow(2.0 * pi * S * S, -1.5);
+  k->A = (R)(1.0 - 3.0 * dd / (2.0 * S * S));
+  k->B = (R)(dd / (2.0 * S * S * S * S));
+  k->tq = (R)(std::pow(2.0 * pi * SigmaD * SigmaD, -1.5) / (2.0 * SigmaD * SigmaD));
+  k->h3 = (R)((p.L[0] / p.M[0]) * (p.L[1] / p.M[1]) * (p.L[2] / p.M[2]));
+  k->same_width = (SigmaD == S) ? 1 : 0;
+}
+
+int validate(const fcm_params* p, std::string* why) {
+  for (int d = 0; d < 3; ++d) {
+    if (!finite_pos(p->L[d])) { *why = "L must be finite and > 0"; return 0; }
+    if (p->M[d] < 1 || p->M[d] > (1 << 14)) { *why = "M must be in [1, 16384]"; return 0; }
+    if (p->M_G > p->M[d]) { *why = "M_G must not exceed M in any dimension"; return 0; }
+  }
+  if (p->M_G < 1 || p->M_G > 24) { *why = "M_G must be in [1, 24]"; return 0; }
+  if (!finite_pos(p->a)) { *why = "a must be finite and > 0"; return 0; }
+  if (!finite_pos(p->eta)) { *why = "eta must be finite and > 0"; return 0; }
+  const double sg = p->a / std::sqrt(kPi), sD = p->a / std::cbrt(6.0 * std::sqrt(kPi));
+  if (!finite_pos(p->Sigma) || p->Sigma < sg * (1 - 1e-12)) { *why = "Sigma must be >= sigma = a/sqrt(pi)"; return 0; }
+  if (!(p->Sigma_D == 0.0 || (std::isfinite(p->Sigma_D) && p->Sigma_D >= sD * (1 - 1e-12)))) {
+    *why = "Sigma_D must be 0 or >= sigma_D = a/(6 sqrt(pi))^(1/3)";
+    return 0;
+  }
+  if (p->precision != FCM_FP32 && p->precision != FCM_FP64) { *why = "precision must be FCM_FP32 or FCM_FP64"; return 0; }
+  if (p->max_n < 0) { *why = "max_n must be >= 0"; return 0; }
+  return 1;
+}
+
+int fold_pending(fcm_handle* h) {
+  for (int idx : h->pending) {
+    StageEvents& ev = h->pool[idx];
+    FCM_CUDA(cudaEventSynchronize(ev.b));
+    float t = 0.f;
+    FCM_CUDA(cudaEventElapsedTime(&t, ev.a, ev.b));
+    h->ms[ev.stage] += t;
+    h->counts[ev.stage] += 1;
+  }
+  h->pending.clear();
+  h->next_event = 0;
+  return FCM_OK;
+}
+
+// Stage timing: stage_begin records the start event of a free pair and returns
+// its slot (-1 when timing is off); stage_end records the stop event.
+int stage_begin(fcm_handle* h, int stage, cudaStream_t s, int* slot) {
+  *slot = -1;
+  if (!h->timing) return FCM_OK;
+  if (h->next_event >= h->pool.size()) {
+    int rc = fold_pending(h);
+    if (rc) return rc;
+  }
+  StageEvents& ev = h->pool[h->next_event];
+  ev.stage = stage;
+  FCM_CUDA(cudaEventRecord(ev.a, s));
+  *slot = (int)h->next_event++;
+  return FCM_OK;
+}
+
+int stage_end(fcm_handle* h, int slot, cudaStream_t s) {
+  if (slot < 0) return FCM_OK;
+  FCM_CUDA(cudaEventRecord(h->pool[slot].b, s));
+  h->pending.push_back(slot);
+  return FCM_OK;
+}
+
+template <typename R>
+int run(fcm_handle* h, int n, const R* pos, const R* F, const R* T, R* U, R* W, int stages, bool spread_only,
+        cudaStream_t s) {
+  const bool torque = (T != nullptr) || (W != nullptr);
+  R* Wout = W ? W : (torque ? (R*)h->wscratch : nullptr);
+  const bool grid_on = spread_only || (stages & FCM_STAGE_GRID);
+  const bool pair_on = !spread_only && (stages & FCM_STAGE_PAIR) && h->pairs_on;
+  const Geometry<R>& g = *reinterpret_cast<const Geometry<R>*>(h->fp64 ? (const void*)&h->gd : (const void*)&h->gf);
+  int rc, t_all, t_bin, t_pair, t_spread, t_fft, t_gather;
+  if ((rc = stage_begin(h, 5, s, &t_all))) return rc;
+  if ((rc = stage_begin(h, 0, s, &t_bin))) return rc;
+  launch_binning<R>(g, n, pos, F, T, h->bb, pair_on, s, &h->launches);
+  if ((rc = stage_end(h, t_bin, s))) return rc;
+  FCM_CUDA(cudaGetLastError());
+  if (pair_on) {
+    R* up = grid_on ? (R*)h->upair : U;
+    R* wp = grid_on ? (R*)h->wpair : Wout;
+    FCM_CUDA(cudaEventRecord(h->ev_fork, s));
+    FCM_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+    if ((rc = stage_begin(h, 4, h->side, &t_pair))) return rc;
+    if (h->fp64)
+      launch_pair_f64(h->gd, h->pd, torque, h->bb, n, (double*)up, (double*)wp, h->side, &h->launches);
+    else
+      launch_pair_f32(h->gf, h->pf, torque, h->bb, n, (float*)up, (float*)wp, h->side, &h->launches);
+    if ((rc = stage_end(h, t_pair, h->side))) return rc;
+    FCM_CUDA(cudaGetLastError());
+    FCM_CUDA(cudaEventRecord(h->ev_join, h->side));
+  }
+  if (grid_on) {
+    launch_zero(h->grid, h->grid_bytes, s, &h->launches);
+    if ((rc = stage_begin(h, 1, s, &t_spread))) return rc;
+    if (h->fp64)
+      launch_spread_f64(h->gd, h->kd, torque, h->bb, n, (double*)h->grid, s, &h->launches);
+    else
+      launch_spread_f32(h->gf, h->kf, torque, h->bb, (float*)h->grid, s, &h->launches);
+    if ((rc = stage_end(h, t_spread, s))) return rc;
+    FCM_CUDA(cudaGetLastError());
+    if (!spread_only) {
+      if ((rc = stage_begin(h, 2, s, &t_fft))) return rc;
+      FCM_CUFFT(cufftSetStream(h->r2c, s));
+      FCM_CUFFT(cufftSetStream(h->c2r, s));
+      if (h->fp64) {
+        FCM_CUFFT(cufftExecD2Z(h->r2c, (cufftDoubleReal*)h->grid, (cufftDoubleComplex*)h->spec));
+        launch_projection<double>(h->gd, h->p.eta, h->spec, s, &h->launches);
+        FCM_CUFFT(cufftExecZ2D(h->c2r, (cufftDoubleComplex*)h->spec, (cufftDoubleReal*)h->grid));
+      } else {
+        FCM_CUFFT(cufftExecR2C(h->r2c, (cufftReal*)h->grid, (cufftComplex*)h->spec));
+        launch_projection<float>(h->gf, (float)h->p.eta, h->spec, s, &h->launches);
+        FCM_CUFFT(cufftExecC2R(h->c2r, (cufftComplex*)h->spec, (cufftReal*)h->grid));
+      }
+      if ((rc = stage_end(h, t_fft, s))) return rc;
+      FCM_CUDA(cudaGetLastError());
+      if (pair_on) FCM_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
+      if ((rc = stage_begin(h, 3, s, &t_gather))) return rc;
+      const R* up = pair_on ? (const R*)h->upair : nullptr;
+      const R* wp = pair_on ? (const R*)h->wpair : nullptr;
+      if (h->fp64)
+        launch_gather_f64(h->gd, h->kd, torque, h->bb, n, (const double*)h->grid, (const double*)up,
+                          (const double*)wp, (double*)U, (double*)Wout, s, &h->launches);
+      else
+        launch_gather_f32(h->gf, h->kf, torque, h->bb, (const float*)h->grid, (const float*)up,
+                          (const float*)wp, (float*)U, (float*)Wout, s, &h->launches);
+      if ((rc = stage_end(h, t_gather, s))) return rc;
+      FCM_CUDA(cudaGetLastError());
+    }
+  } else if (pair_on) {
+    FCM_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
+  } else if (!spread_only) {  // only the correction requested and it is identically zero
+    launch_zero(U, sizeof(R) * 3 * (size_t)n, s, &h->launches);
+    if (W) launch_zero(W, sizeof(R) * 3 * (size_t)n, s, &h->launches);
+  }
+  if ((rc = stage_end(h, t_all, s))) return rc;
+  FCM_CUDA(cudaGetLastError());
+  return FCM_OK;
+}
+
+int apply_common(fcm_handle* h, int n, const void* pos, const void* F, const void* T, void* U, void* W,
+                 int stages, bool spread_only, void* stream) {
+  if (!h) return fail(FCM_ERR_ARG, "handle is NULL");
+  if (n < 0 || n > h->p.max_n)
+    return fail(FCM_ERR_ARG, "n = " + std::to_string(n) + " outside [0, max_n = " + std::to_string(h->p.max_n) + "]");
+  if (n > 0 && (!pos || !F || (!spread_only && !U)))
+    return fail(FCM_ERR_ARG, "pos, F and U must be non-NULL when n > 0");
+  if (stages < 1 || stages > FCM_STAGE_ALL) return fail(FCM_ERR_ARG, "stages must be a non-empty subset of FCM_STAGE_ALL");
+  if (n == 0) return FCM_OK;
+  DeviceGuard guard(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (h->fp64)
+    return run<double>(h, n, (const double*)pos, (const double*)F, (const double*)T, (double*)U, (double*)W,
+                       stages, spread_only, s);
+  return run<float>(h, n, (const float*)pos, (const float*)F, (const float*)T, (float*)U, (float*)W, stages,
+                    spread_only, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+int fcm_version(void) { return 10000; }
+
+int fcm_params_default(fcm_params* p) {
+  if (!p) return fail(FCM_ERR_ARG, "params is NULL");
+  std::memset(p, 0, sizeof(*p));
+  p->a = 1.0;
+  p->eta = 1.0;
+  p->precision = FCM_FP32;
+  return FCM_OK;
+}
+
+int fcm_create(const fcm_params* p, int device, fcm_handle** out) {
+  if (!out) return fail(FCM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!p) return fail(FCM_ERR_ARG, "params is NULL");
+  std::string why;
+  if (!validate(p, &why)) return fail(FCM_ERR_ARG, why);
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return fail(FCM_ERR_CUDA, "CUDA device " + std::to_string(device) + " is not available");
+  }
+  const double sg = p->a / std::sqrt(kPi), sD = p->a / std::cbrt(6.0 * std::sqrt(kPi));
+  const double SigmaD = (p->Sigma_D == 0.0) ? p->Sigma : p->Sigma_D;
+  const bool pairs_on = (p->Sigma > sg * (1 + 1e-12)) || (SigmaD > sD * (1 + 1e-12));
+  if (pairs_on) {
+    const double Lmin = std::min(p->L[0], std::min(p->L[1], p->L[2]));
+    if (!(p->r_c > 0) || !(p->r_c <= 0.5 * Lmin)) return fail(FCM_ERR_ARG, "r_c must satisfy 0 < r_c <= min(L)/2");
+  }
+  fcm_handle* h = new fcm_handle();
+  h->p = *p;
+  h->p.Sigma_D = SigmaD;
+  h->device = device;
+  h->fp64 = (p->precision == FCM_FP64);
+  h->pairs_on = pairs_on;
+  DeviceGuard guard(device);
+  int tile[3];
+  if (h->fp64) { tile[0] = tile[1] = tile[2] = std::min(8, std::min(p->M[0], std::min(p->M[1], p->M[2]))); }
+  else choose_tile(*p, tile);
+  for (int d = 0; d < 3; ++d) h->p.tile[d] = tile[d];
+  fill_geometry(h->p, tile, &h->gf);
+  fill_geometry(h->p, tile, &h->gd);
+  fill_kernel_consts(h->p, SigmaD, &h->kf);
+  fill_kernel_consts(h->p, SigmaD, &h->kd);
+  make_pair_consts(p->a, p->eta, p->Sigma, SigmaD, pairs_on ? p->r_c : 0.0, 0.5 * sg, &h->pd);
+  narrow_pair_consts(h->pd, &h->pf);
+  if (!h->fp64 && tile_smem_bytes(tile, p->M_G) > (size_t)tile_smem_limit()) {
+    release(h);
+    return fail(FCM_ERR_ARG, "M_G too large for the FP32 tile kernels");
+  }
+  int rc = FCM_OK;
+  auto A = [&](void** q, size_t bytes) { if (rc == FCM_OK) rc = halloc(h, q, bytes); };
+  const size_t n = (size_t)std::max(p->max_n, 1);
+  const size_t rsz = h->fp64 ? sizeof(double) : sizeof(float);
+  const size_t v4 = h->fp64 ? sizeof(Vec4<double>) : sizeof(Vec4<float>);
+  const size_t mtot = (size_t)p->M[0] * p->M[1] * p->M[2];
+  const size_t ncplx = (size_t)(p->M[0] / 2 + 1) * p->M[1] * p->M[2];
+  BinBuffers& b = h->bb;
+  b.ntiles = h->gf.ntile[0] * h->gf.ntile[1] * h->gf.ntile[2];
+  b.ncells = pairs_on ? h->gf.mcell[0] * h->gf.mcell[1] * h->gf.mcell[2] : 1;
+  if ((size_t)b.ncells > (1u << 26)) { release(h); return fail(FCM_ERR_ARG, "too many pair cells (r_c too small for L)"); }
+  A((void**)&b.tile_key, 4 * n); A((void**)&b.tile_rank, 4 * n);
+  A((void**)&b.cell_key, 4 * n); A((void**)&b.cell_rank, 4 * n);
+  A((void**)&b.tile_count, 4 * (size_t)(b.ntiles + 1)); A((void**)&b.tile_start, 4 * (size_t)(b.ntiles + 1));
+  A((void**)&b.cell_count, 4 * (size_t)(b.ncells + 1)); A((void**)&b.cell_start, 4 * (size_t)(b.ncells + 1));
+  A(&b.t_pos, v4 * n); A(&b.t_F, v4 * n); A(&b.t_T, v4 * n);
+  A(&b.c_pos, v4 * n); A(&b.c_F, v4 * n); A(&b.c_T, v4 * n);
+  A((void**)&b.status, 256);
+  A(&h->upair, 3 * rsz * n); A(&h->wpair, 3 * rsz * n); A(&h->wscratch, 3 * rsz * n);
+  h->grid_bytes = 3 * rsz * mtot;
+  A(&h->grid, h->grid_bytes);
+  A(&h->spec, 3 * 2 * rsz * ncplx);
+  if (rc != FCM_OK) { std::string e = g_error; release(h); return fail(rc, e); }
+  cudaError_t ce = cudaMemset(b.tile_count, 0, 4 * (size_t)(b.ntiles + 1));
+  if (ce == cudaSuccess) ce = cudaMemset(b.cell_count, 0, 4 * (size_t)(b.ncells + 1));
+  if (ce == cudaSuccess) ce = cudaMemset(b.status, 0, 256);
+  if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+  if (ce != cudaSuccess) { release(h); return fail(FCM_ERR_CUDA, std::string("setup: ") + cudaGetErrorString(ce)); }
+  int dims[3] = {p->M[2], p->M[1], p->M[0]};
+  cufftResult fr = cufftPlanMany(&h->r2c, 3, dims, nullptr, 1, (int)mtot, nullptr, 1, (int)ncplx,
+                                 h->fp64 ? CUFFT_D2Z : CUFFT_R2C, 3);
+  if (fr == CUFFT_SUCCESS) {
+    fr = cufftPlanMany(&h->c2r, 3, dims, nullptr, 1, (int)ncplx, nullptr, 1, (int)mtot,
+                       h->fp64 ? CUFFT_Z2D : CUFFT_C2R, 3);
+    if (fr != CUFFT_SUCCESS) cufftDestroy(h->r2c);
+  }
+  if (fr != CUFFT_SUCCESS) { release(h); return fail(FCM_ERR_CUFFT, "cufftPlanMany failed: " + std::to_string((int)fr)); }
+  h->plans = true;
+  size_t ws = 0;
+  if (cufftGetSize(h->r2c, &ws) == CUFFT_SUCCESS) h->bytes += ws;
+  if (cufftGetSize(h->c2r, &ws) == CUFFT_SUCCESS) h->bytes += ws;
+  if (cudaDeviceSynchronize() != cudaSuccess) { release(h); return fail(FCM_ERR_CUDA, "setup synchronisation failed"); }
+  *out = h;
+  return FCM_OK;
+}
+
+int fcm_destroy(fcm_handle* h) {
+  release(h);
+  return FCM_OK;
+}
+
+int fcm_apply(fcm_handle* h, int n, const void* pos, const void* F, const void* T, void* U, void* W, void* stream) {
+  return apply_common(h, n, pos, F, T, U, W, FCM_STAGE_ALL, false, stream);
+}
+
+int fcm_apply_stages(fcm_handle* h, int n, const void* pos, const void* F, const void* T, void* U, void* W,
+                     int stages, void* stream) {
+  return apply_common(h, n, pos, F, T, U, W, stages, false, stream);
+}
+
+int fcm_spread(fcm_handle* h, int n, const void* pos, const void* F, const void* T, void* stream) {
+  return apply_common(h, n, pos, F, T, nullptr, nullptr, FCM_STAGE_GRID, true, stream);
+}
+
+int fcm_copy_grid(fcm_handle* h, void* dst, void* stream) {
+  if (!h || !dst) return fail(FCM_ERR_ARG, "handle and dst must be non-NULL");
+  DeviceGuard guard(h->device);
+  FCM_CUDA(cudaMemcpyAsync(dst, h->grid, h->grid_bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return FCM_OK;
+}
+
+int fcm_check(fcm_handle* h, void* stream, int timeout_ms, int* flags) {
+  if (!h) return fail(FCM_ERR_ARG, "handle is NULL");
+  DeviceGuard guard(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t ev;
+  FCM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  cudaEventRecord(ev, s);
+  cudaEventRecord(h->ev_fork, h->side);
+  auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t a = cudaEventQuery(ev), b = cudaEventQuery(h->ev_fork);
+    if (a == cudaSuccess && b == cudaSuccess) break;
+    if ((a != cudaSuccess && a != cudaErrorNotReady) || (b != cudaSuccess && b != cudaErrorNotReady)) {
+      cudaEventDestroy(ev);
+      return fail(FCM_ERR_CUDA, std::string("device error: ") + cudaGetErrorString(a != cudaSuccess && a != cudaErrorNotReady ? a : b));
+    }
+    auto el = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
+    if (el > timeout_ms) {
+      cudaEventDestroy(ev);
+      return fail(FCM_ERR_TIMEOUT, "work did not finish within " + std::to_string(timeout_ms) + " ms");
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  cudaEventDestroy(ev);
+  int v = 0;
+  FCM_CUDA(cudaMemcpy(&v, h->bb.status, sizeof(int), cudaMemcpyDeviceToHost));
+  FCM_CUDA(cudaMemset(h->bb.status, 0, sizeof(int)));
+  if (flags) *flags = v;
+  if (v) return fail(FCM_ERR_INPUT, "non-finite particle position seen");
+  return FCM_OK;
+}
+
+int fcm_set_timing(fcm_handle* h, int enable) {
+  if (!h) return fail(FCM_ERR_ARG, "handle is NULL");
+  DeviceGuard guard(h->device);
+  if (enable && h->pool.empty()) {
+    h->pool.resize(6 * 256);
+    for (auto& ev : h->pool) {
+      FCM_CUDA(cudaEventCreate(&ev.a));
+      FCM_CUDA(cudaEventCreate(&ev.b));
+    }
+  }
+  h->timing = enable != 0;
+  return FCM_OK;
+}
+
+int fcm_read_timing(fcm_handle* h, double* ms, long long* counts) {
+  if (!h || !ms || !counts) return fail(FCM_ERR_ARG, "handle, ms and counts must be non-NULL");
+  DeviceGuard guard(h->device);
+  int rc = fold_pending(h);
+  if (rc) return rc;
+  for (int k = 0; k < FCM_NUM_STAGES; ++k) {
+    ms[k] = h->ms[k];
+    counts[k] = h->counts[k];
+    h->ms[k] = 0.0;
+    h->counts[k] = 0;
+  }
+  return FCM_OK;
+}
+
+long long fcm_launch_count(const fcm_handle* h) { return h ? h->launches : 0; }
+
+size_t fcm_workspace_bytes(const fcm_handle* h) { return h ? h->bytes : 0; }
+
+int fcm_cutoff_radius(double Sigma, double Sigma_D, double a, double eta, double tol, int torques, double* r_c) {
+  if (!r_c) return fail(FCM_ERR_ARG, "r_c is NULL");
+  if (!(a > 0) || !(eta > 0) || !(tol > 0) || !(Sigma > 0)) return fail(FCM_ERR_ARG, "a, eta, tol, Sigma must be > 0");
+  if (Sigma_D == 0.0) Sigma_D = Sigma;
+  PairConsts<double> C;
+  make_pair_consts(a, eta, Sigma, Sigma_D, 1e300, 0.0, &C);
+  const double pi = kPi;
+  const double nvf = 6 * pi * eta * a, nwt = 8 * pi * eta * a * a * a, nwf = std::sqrt(nvf * nwt);
+  auto norm = [&](double r) {
+    double al, bt, cr, gm, dl;
+    pair_coeffs<double>(r * r, C, al, bt, cr, gm, dl);
+    double v = std::max(std::fabs(al), std::fabs(al + bt * r * r)) * nvf;
+    if (torques) {
+      v = std::max(v, std::max(std::fabs(gm), std::fabs(gm + dl * r * r)) * nwt);
+      v = std::max(v, std::fabs(cr) * r * nwf);
+    }
+    return v;
+  };
+  const double rmax = 40.0 * std::max(Sigma, Sigma_D);
+  const int steps = 40000;
+  double prev = rmax;
+  double lo = -1, hi = -1;
+  for (int k = 0; k < steps; ++k) {
+    double r = rmax - (rmax - 1e-3) * k / (steps - 1);
+    if (norm(r) >= tol) {
+      if (k == 0) return fail(FCM_ERR_ARG, "correction still above tol at 40 Sigma");
+      lo = r;
+      hi = prev;
+      break;
+    }
+    prev = r;
+  }
+  if (lo < 0) { *r_c = 0.0; return FCM_OK; }
+  for (int it = 0; it < 80; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (norm(mid) >= tol) lo = mid; else hi = mid;
+  }
+  *r_c = hi;
+  return FCM_OK;
+}
+
+const char* fcm_last_error(void) { return g_error.c_str(); }
+
+}  // extern "C"

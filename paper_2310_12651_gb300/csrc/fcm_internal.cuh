@@ -1,0 +1,233 @@
+// Internal declarations of libfcm: device parameter blocks, index rules, the
+// pairwise-correction closed forms and the kernel launchers of each stage.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <math.h>
+
+namespace fcm {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kSeriesTerms = 10;   // Taylor terms of the small-r branch
+constexpr int kMaxMG = 24;         // largest grid support the kernels accept
+
+// Status bits written by kernels into the handle's device status word.
+enum : int { kStatusNonFinite = 1 };
+
+// ---------------------------------------------------------------- vectors
+template <typename R> struct Vec4;
+template <> struct alignas(16) Vec4<float> { float x, y, z, w; };
+template <> struct alignas(32) Vec4<double> { double x, y, z, w; };
+
+__host__ __device__ inline float as_real_bits(int i, float) {
+#ifdef __CUDA_ARCH__
+  return __int_as_float(i);
+#else
+  union { int i; float f; } u; u.i = i; return u.f;
+#endif
+}
+__host__ __device__ inline double as_real_bits(int i, double) { return (double)i; }
+__device__ inline int index_from_w(float w) { return __float_as_int(w); }
+__device__ inline int index_from_w(double w) { return (int)w; }
+
+// ---------------------------------------------------------------- math wrappers
+__host__ __device__ inline float  x_erfc(float v)  { return erfcf(v); }
+__host__ __device__ inline double x_erfc(double v) { return erfc(v); }
+__host__ __device__ inline float  x_exp(float v)   { return expf(v); }
+__host__ __device__ inline double x_exp(double v)  { return exp(v); }
+__host__ __device__ inline float  x_sqrt(float v)  { return sqrtf(v); }
+__host__ __device__ inline double x_sqrt(double v) { return sqrt(v); }
+__host__ __device__ inline float  x_floor(float v) { return floorf(v); }
+__host__ __device__ inline double x_floor(double v){ return floor(v); }
+__device__ inline float  x_mul_rn(float a, float b)   { return __fmul_rn(a, b); }
+__device__ inline double x_mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
+// ---------------------------------------------------------------- geometry
+// Everything the index rules need, in the handle's precision.
+template <typename R>
+struct Geometry {
+  R L[3];        // box edges
+  R h[3];        // grid spacing L_i / M_i
+  R cellw_inv[3];// m_i / L_i (pair cells)
+  int M[3];      // grid points
+  int MG;        // grid support per dimension
+  int tile[3];   // spread/gather tile in grid points
+  int ntile[3];  // ceil(M_i / tile_i)
+  int mcell[3];  // pair cells per dimension, max(int(L_i / r_c), 3)
+};
+
+// Position wrapped into [0, L): y - L floor(y / L), with the product rounded on
+// its own so the value does not depend on contraction into an FMA.
+template <typename R>
+__device__ inline R wrap_coord(R y, R L, int* bad) {
+  if (!(y == y) || y - y != R(0)) { *bad = 1; return R(0); }   // NaN or +-inf
+  R w = y - x_mul_rn(L, x_floor(y / L));
+  if (w >= L) w -= L;
+  if (w < R(0)) w = R(0);
+  return w;
+}
+
+// First grid index of the M_G-point window: floor(y/h - M_G/2) + 1 (unwrapped).
+template <typename R>
+__device__ inline int window_start(R y, R h, int MG) {
+  R v = x_floor(y / h - R(0.5) * R(MG));
+  v = fmax(fmin(v, R(1 << 29)), R(-(1 << 29)));
+  return (int)v + 1;
+}
+
+__host__ __device__ inline int pmod(int i, int m) { int r = i % m; return r < 0 ? r + m : r; }
+
+template <typename R>
+__device__ inline int cell_coord(R yw, R winv, int m) {
+  int c = (int)(yw * winv);
+  return c < 0 ? 0 : (c >= m ? m - 1 : c);
+}
+
+// ---------------------------------------------------------------- kernel constants
+// Spread/gather constants of the modified kernels (Section 3.1 and 3.4):
+//   Delta~(d; Sigma) = nrm exp(-|d|^2/(2 Sigma^2)) (A + B |d|^2),
+//   A = 1 - 3 dd / (2 Sigma^2), B = dd / (2 Sigma^4), dd = sigma^2 - Sigma^2;
+//   torque part  -(1/2) T x grad Delta(d; Sigma_D) = nrmD/(2 Sigma_D^2) exp(..) (T x d).
+template <typename R>
+struct KernelConsts {
+  R inv2S2;      // 1 / (2 Sigma^2)
+  R inv2SD2;     // 1 / (2 Sigma_D^2)
+  R nrm;         // (2 pi Sigma^2)^-3/2
+  R A, B;
+  R tq;          // (2 pi Sigma_D^2)^-3/2 / (2 Sigma_D^2)
+  R h3;          // h_x h_y h_z
+  int same_width;// Sigma_D == Sigma
+};
+
+// ---------------------------------------------------------------- pair correction
+// Radial form of the correction blocks (Section 3.2, 3.4), x = Y_n - Y_m:
+//   M_VF - M~_VF = al I + bt x x^T
+//   M_WF - M~_WF = M_VT - M~_VT = cr (-x cross)
+//   M_WT - M~_WT = gm I + dl x x^T
+// For r^2 < rs2 the coefficients come from their Taylor series in r^2, whose
+// terms are Gaussian moments of the Fourier kernels (no cancellation at small r);
+// at r = 0 the series gives the Appendix B self corrections.
+template <typename R>
+struct PairConsts {
+  R eta;
+  R sg2, Sg2, dd;                  // sigma^2, Sigma^2, sigma^2 - Sigma^2
+  R inv2sg, inv2Sg;                // 1/(2 sigma), 1/(2 Sigma)
+  R nA, eA, nB, eB;                // Delta(r; sigma sqrt2), Delta(r; Sigma sqrt2): n exp(-e r^2)
+  R sg4, Sg4;
+  R k1, k2;                        // 1/(s1 sqrt2), 1/(s2 sqrt2), s1^2 = sigma^2 + sigma_D^2, s2^2 = Sigma^2 + Sigma_D^2
+  R s1sq, s2sq, n1, e1, n2, e2;    // Delta(r; s1), Delta(r; s2)
+  R inv2sD, inv2SD;                // 1/(2 sigma_D), 1/(2 Sigma_D)
+  R sD2, SD2;                      // sigma_D^2, Sigma_D^2
+  R nDa, eDa, nDb, eDb;            // Delta(r; sigma_D sqrt2), Delta(r; Sigma_D sqrt2)
+  R selfVF, selfWT;                // Appendix B
+  R rs2;                           // series below this r^2
+  R rc2;                           // cutoff squared
+  R ser_al[kSeriesTerms], ser_bt[kSeriesTerms], ser_cr[kSeriesTerms];
+  R ser_gm[kSeriesTerms], ser_dl[kSeriesTerms];
+};
+
+template <typename R>
+__host__ __device__ inline R horner(const R* c, R x) {
+  R s = c[kSeriesTerms - 1];
+#pragma unroll
+  for (int j = kSeriesTerms - 2; j >= 0; --j) s = s * x + c[j];
+  return s;
+}
+
+template <typename R>
+__host__ __device__ inline void pair_coeffs(R r2, const PairConsts<R>& C, R& al, R& bt, R& cr,
+                                            R& gm, R& dl) {
+  if (r2 < C.rs2) {
+    al = horner(C.ser_al, r2);
+    bt = horner(C.ser_bt, r2);
+    cr = horner(C.ser_cr, r2);
+    gm = horner(C.ser_gm, r2);
+    dl = horner(C.ser_dl, r2);
+    return;
+  }
+  const R pi = R(kPi);
+  R r = x_sqrt(r2);
+  R ir = R(1) / r, ir2 = ir * ir, ir3 = ir2 * ir;
+  R ieta = R(1) / C.eta;
+  // VF: (G + sigma^2 lap G)(erf(r/2sigma) - erf(r/2Sigma)) + S3 terms - dd Q2 - dd^2/4 T
+  R E = x_erfc(r * C.inv2Sg) - x_erfc(r * C.inv2sg);
+  R DA = C.nA * x_exp(-r2 * C.eA);
+  R DB = C.nB * x_exp(-r2 * C.eB);
+  R t1 = E * ir * ieta / (R(8) * pi);
+  R t2 = E * C.sg2 * ir3 * ieta / (R(4) * pi);
+  R s3 = (C.sg4 * DA - C.Sg4 * DB) * ir2 * ieta;
+  R q = C.dd * DB * ieta;
+  R tt = C.dd * C.dd * DB * ieta / (R(8) * C.Sg2);
+  R rho = r2 / (R(2) * C.Sg2);
+  al = t1 + t2 - R(2) * s3 + q * (R(1) + R(2) * C.Sg2 * ir2) - tt * (R(2) - rho);
+  R be = t1 - R(3) * t2 + R(6) * s3 - q * (R(1) + R(6) * C.Sg2 * ir2) - tt * rho;
+  bt = be * ir2;
+  // WF: R(x; s1) - R(x; s2) - dd/2 K(x; s2)
+  R Ef = x_erfc(r * C.k2) - x_erfc(r * C.k1);
+  R D1 = C.n1 * x_exp(-r2 * C.e1);
+  R D2 = C.n2 * x_exp(-r2 * C.e2);
+  cr = (Ef - R(4) * pi * r * (C.s1sq * D1 - C.s2sq * D2)) * ir3 * ieta / (R(8) * pi)
+       + R(0.5) * C.dd * D2 * ieta / (R(2) * C.s2sq);
+  // WT: (P(x; sigma_D sqrt2) - P(x; Sigma_D sqrt2)) / 2
+  R Et = x_erfc(r * C.inv2SD) - x_erfc(r * C.inv2sD);
+  R Da = C.nDa * x_exp(-r2 * C.eDa);
+  R Db = C.nDb * x_exp(-r2 * C.eDb);
+  R w1 = Et * ir3 * ieta / (R(8) * pi);
+  R w2 = ir2 * ieta * R(0.5);
+  gm = R(0.5) * (-w1 + ((R(2) * C.sD2 + r2) * Da - (R(2) * C.SD2 + r2) * Db) * w2);
+  R de = R(0.5) * (R(3) * w1 - ((R(6) * C.sD2 + r2) * Da - (R(6) * C.SD2 + r2) * Db) * w2);
+  dl = de * ir2;
+}
+
+// Host-side construction of the constants (double), then narrowing.
+void make_pair_consts(double a, double eta, double Sigma, double Sigma_D, double r_c,
+                      double r_series, PairConsts<double>* out);
+void narrow_pair_consts(const PairConsts<double>& in, PairConsts<float>* out);
+
+// ---------------------------------------------------------------- launch API
+// Binning: wraps positions, computes tile and cell keys, counts and ranks,
+// scans, then scatters pos/F/T into tile-sorted and cell-sorted Vec4 arrays
+// whose w field carries the original index.
+struct BinBuffers {
+  unsigned* tile_key; unsigned* tile_rank; unsigned* cell_key; unsigned* cell_rank;
+  int* tile_count; int* tile_start; int* cell_count; int* cell_start;
+  int ntiles; int ncells;
+  void* t_pos; void* t_F; void* t_T;   // tile-sorted Vec4<R>
+  void* c_pos; void* c_F; void* c_T;   // cell-sorted Vec4<R>
+  int* status;
+};
+
+template <typename R>
+void launch_binning(const Geometry<R>& g, int n, const R* pos, const R* F, const R* T,
+                    const BinBuffers& b, bool need_cells, cudaStream_t s, long long* launches);
+
+template <typename R>
+void launch_projection(const Geometry<R>& g, R eta, void* spectrum, cudaStream_t s, long long* launches);
+
+// FP32 tiled spread / gather (shared-memory tile accumulation, halo flush).
+size_t tile_smem_bytes(const int tile[3], int MG);
+int tile_smem_limit();
+void launch_spread_f32(const Geometry<float>& g, const KernelConsts<float>& kc, bool torque,
+                       const BinBuffers& b, float* grid, cudaStream_t s, long long* launches);
+void launch_gather_f32(const Geometry<float>& g, const KernelConsts<float>& kc, bool torque,
+                       const BinBuffers& b, const float* grid, const float* upair, const float* wpair,
+                       float* U, float* W, cudaStream_t s, long long* launches);
+void launch_pair_f32(const Geometry<float>& g, const PairConsts<float>& pc, bool torque,
+                     const BinBuffers& b, int n, float* upair, float* wpair, cudaStream_t s,
+                     long long* launches);
+
+// FP64 plain path (block per particle, global FP64 atomics; thread per particle pairs).
+void launch_spread_f64(const Geometry<double>& g, const KernelConsts<double>& kc, bool torque,
+                       const BinBuffers& b, int n, double* grid, cudaStream_t s, long long* launches);
+void launch_gather_f64(const Geometry<double>& g, const KernelConsts<double>& kc, bool torque,
+                       const BinBuffers& b, int n, const double* grid, const double* upair,
+                       const double* wpair, double* U, double* W, cudaStream_t s, long long* launches);
+void launch_pair_f64(const Geometry<double>& g, const PairConsts<double>& pc, bool torque,
+                     const BinBuffers& b, int n, double* upair, double* wpair, cudaStream_t s,
+                     long long* launches);
+
+// Zero-fill of a device range (a kernel of this library, counted as a launch).
+void launch_zero(void* p, size_t bytes, cudaStream_t s, long long* launches);
+
+}  // namespace fcm

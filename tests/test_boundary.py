@@ -1,0 +1,77 @@
+"""The C-ABI library without a GPU: it loads, exports every declared symbol,
+rejects bad parameters on the host, and its host-side cutoff rule agrees with
+the oracle's (no kernel runs here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from oracle import params as oracle_params
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def fcm():
+    from paper_2310_12651_gb300 import build
+    build.build()
+    from paper_2310_12651_gb300 import fcm as mod
+    return mod
+
+
+def _declared_functions():
+    text = open(os.path.join(ROOT, "include", "fcm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fcm_[a-z_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(fcm):
+    lib = ctypes.CDLL(fcm.LIB_PATH)
+    names = _declared_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(fcm.EXPORTED)
+
+
+def test_params_struct_matches_header(fcm):
+    text = open(os.path.join(ROOT, "include", "fcm.h")).read()
+    body = re.search(r"typedef struct fcm_params \{(.*?)\} fcm_params;", text, re.S).group(1)
+    fields = re.findall(r"^\s*(?:double|int)\s+(\w+)", body, re.M)
+    assert fields == [f[0] for f in fcm.Params._fields_]
+    assert ctypes.sizeof(fcm.Params) == 3 * 8 + 3 * 4 + 4 + 5 * 8 + 3 * 4 + 3 * 4
+
+
+@pytest.mark.parametrize("change, message", [
+    (dict(Sigma=0.3), "Sigma must be >= sigma"),
+    (dict(M_G=80), "M_G"),
+    (dict(M_G=0), "M_G"),
+    (dict(r_c=60.0), "r_c"),
+    (dict(r_c=0.0), "r_c"),
+    (dict(eta=-1.0), "eta"),
+    (dict(L=float("nan")), "L must"),
+    (dict(precision=7), "precision"),
+    (dict(Sigma_D=0.1), "Sigma_D"),
+])
+def test_invalid_parameters_are_rejected_on_the_host(fcm, change, message):
+    kw = dict(L=100.0, M=64, Sigma=2.0, r_c=16.9, M_G=12, max_n=10)
+    kw.update(change)
+    p = fcm.make_params(**kw)
+    with pytest.raises(fcm.FcmError) as e:
+        fcm.Handle(p)
+    assert e.value.code in (fcm.FCM_ERR_ARG, fcm.FCM_ERR_CUDA)
+    if e.value.code == fcm.FCM_ERR_ARG:
+        assert message in str(e.value)
+
+
+@pytest.mark.parametrize("Sigma, tol, torques", [(2.0, 1e-8, False), (2.0, 1e-6, True), (1.5, 1e-4, True),
+                                                 (3.0, 1e-6, False), (0.9, 1e-10, True)])
+def test_cutoff_rule_matches_oracle(fcm, Sigma, tol, torques):
+    ours = fcm.cutoff_radius(Sigma, tol, torques=torques)
+    ref = oracle_params.cutoff_radius(Sigma, tol, torques=torques)
+    assert abs(ours - ref) < 1e-6 * ref
+
+
+def test_last_error_is_a_message(fcm):
+    assert isinstance(fcm.library().fcm_last_error(), bytes)

@@ -278,3 +278,15 @@ def test_grid_error_against_table1():
         U, _ = g.fast_fcm_apply(Y, F, None, L, M, MG, Sigma, rc)
         err = np.mean(np.linalg.norm(U - Ub, axis=1) / np.linalg.norm(Ub, axis=1))
         assert eps / 2 <= err <= 2 * eps, (eps, err)
+
+
+def test_pair_correction_subset_equals_full_rows():
+    L, n = 24.0, 150
+    Y = inputs.random_suspension(n, L, 17)
+    F, T = inputs.random_loads(n, 18)
+    Sigma, rc = 1.4, 9.5
+    Uf, Wf = g.pair_correction(Y, F, T, L, rc, Sigma, Sigma)
+    idx = np.array([0, 7, 33, 149])
+    Us, Ws = g.pair_correction_subset(Y, F, T, L, rc, Sigma, Sigma, idx)
+    np.testing.assert_allclose(Us, Uf[idx], rtol=1e-12, atol=1e-16)
+    np.testing.assert_allclose(Ws, Wf[idx], rtol=1e-12, atol=1e-16)
