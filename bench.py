@@ -102,7 +102,7 @@ class ClockSampler:
         sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
         smax = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4) if "Active" in r[5 + k]})
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip() == "Active"})
         power = [float(r[3]) for r in rows if r[3].strip().replace(".", "").isdigit()]
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": reasons, "samples": len(rows), "power_w_max": max(power) if power else None}
@@ -206,6 +206,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--spread-kernel", type=int, default=0, help="0 choose, 1 row-stationary, 2 shared atomics")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
@@ -228,7 +229,8 @@ def main():
     w = workload()
     B = args.batch
     n = w["n"]
-    params = fcm.make_params(w["L"], w["M"], w["Sigma"], w["r_c"], w["M_G"], n, fcm.FCM_FP32)
+    params = fcm.make_params(w["L"], w["M"], w["Sigma"], w["r_c"], w["M_G"], n, fcm.FCM_FP32,
+                             spread_kernel=args.spread_kernel)
     h = fcm.Handle(params, local)
     systems = []
     for b in range(B):

@@ -70,6 +70,8 @@ typedef struct fcm_params {
   int precision;     /* fcm_precision                                                    */
   int max_n;         /* capacity: largest n accepted by fcm_apply                         */
   int tile[3];       /* FP32 spread/gather tile in grid points per dimension; 0 = choose */
+  int spread_kernel; /* FP32 spread: 0 = choose, 1 = row-stationary (registers, no      */
+                     /* atomics; needs tile[0] == 8 and M_G <= 16), 2 = shared atomics   */
 } fcm_params;
 
 typedef struct fcm_handle fcm_handle;

@@ -52,7 +52,7 @@ def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = N
         return LIB
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
-    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
+    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2,-fvisibility=hidden", "--expt-relaxed-constexpr",
                     "-I", os.path.join(ROOT, "include")]
     if verbose_ptxas:
         flags += ["-Xptxas", "-v"]

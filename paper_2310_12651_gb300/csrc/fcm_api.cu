@@ -164,6 +164,32 @@ void narrow_pair_consts(const PairConsts<double>& in, PairConsts<float>* o) {
   for (size_t k = 0; k < sizeof(PairConsts<float>) / sizeof(float); ++k) dst[k] = (float)src[k];
 }
 
+void build_pair_table(const PairConsts<double>& pd, double r_lo, double r_hi, float4* coef) {
+  PairConsts<double> c = pd;
+  c.rs2 = 0.0;  // the closed form throughout the tabulated range
+  const int n = kPairTableIntervals;
+  const double h = (r_hi - r_lo) / n;
+  for (int i = 0; i < n; ++i) {
+    double v[4][5];
+    for (int k = 0; k < 4; ++k) {
+      const double r = r_lo + (i + k / 3.0) * h;
+      pair_coeffs<double>(r * r, c, v[k][0], v[k][1], v[k][2], v[k][3], v[k][4]);
+    }
+    for (int f = 0; f < 5; ++f) {
+      // Newton differences on s = 3u in {0, 1, 2, 3}, rewritten in powers of u
+      const double d1 = v[1][f] - v[0][f];
+      const double d2 = v[2][f] - 2.0 * v[1][f] + v[0][f];
+      const double d3 = v[3][f] - 3.0 * v[2][f] + 3.0 * v[1][f] - v[0][f];
+      float4 q;
+      q.x = (float)v[0][f];
+      q.y = (float)(3.0 * (d1 - 0.5 * d2 + d3 / 3.0));
+      q.z = (float)(9.0 * (0.5 * d2 - 0.5 * d3));
+      q.w = (float)(27.0 * d3 / 6.0);
+      coef[5 * i + f] = q;
+    }
+  }
+}
+
 }  // namespace fcm
 
 struct fcm_handle {
@@ -177,6 +203,7 @@ struct fcm_handle {
   KernelConsts<double> kd{};
   PairConsts<float> pf{};
   PairConsts<double> pd{};
+  PairTable ptab{};
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   BinBuffers bb{};
@@ -237,10 +264,21 @@ void release(fcm_handle* h) {
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0; }
 
+// FP32 tile: (8, t, t) with the largest t in {8, 4, 2} whose extended (y, z)
+// rows fit the row-stationary spread; otherwise the largest tile whose
+// extended region fits shared memory (atomic spread).
 void choose_tile(const fcm_params& p, int tile[3]) {
   if (p.tile[0] > 0 && p.tile[1] > 0 && p.tile[2] > 0) {
     for (int d = 0; d < 3; ++d) tile[d] = std::min(p.tile[d], p.M[d]);
     return;
+  }
+  for (int t : {8, 4, 2}) {
+    int c[3] = {std::min(8, p.M[0]), std::min(t, p.M[1]), std::min(t, p.M[2])};
+    if (spread_uses_rows(c, p.M_G) && tile_smem_bytes(c, p.M_G) <= (size_t)tile_smem_limit() &&
+        spread_smem_bytes(c, p.M_G) <= (size_t)tile_smem_limit()) {
+      tile[0] = c[0]; tile[1] = c[1]; tile[2] = c[2];
+      return;
+    }
   }
   static const int cands[][3] = {{8, 8, 8}, {8, 8, 4}, {8, 4, 4}, {4, 4, 4}, {4, 4, 2}, {4, 2, 2},
                                  {2, 2, 2}, {2, 2, 1}, {2, 1, 1}, {1, 1, 1}};
@@ -304,6 +342,7 @@ int validate(const fcm_params* p, std::string* why) {
   }
   if (p->precision != FCM_FP32 && p->precision != FCM_FP64) { *why = "precision must be FCM_FP32 or FCM_FP64"; return 0; }
   if (p->max_n < 0) { *why = "max_n must be >= 0"; return 0; }
+  if (p->spread_kernel < 0 || p->spread_kernel > 2) { *why = "spread_kernel must be 0, 1 or 2"; return 0; }
   return 1;
 }
 
@@ -367,7 +406,7 @@ int run(fcm_handle* h, int n, const R* pos, const R* F, const R* T, R* U, R* W, 
     if (h->fp64)
       launch_pair_f64(h->gd, h->pd, torque, h->bb, n, (double*)up, (double*)wp, h->side, &h->launches);
     else
-      launch_pair_f32(h->gf, h->pf, torque, h->bb, n, (float*)up, (float*)wp, h->side, &h->launches);
+      launch_pair_f32(h->gf, h->pf, h->ptab, torque, h->bb, n, (float*)up, (float*)wp, h->side, &h->launches);
     if ((rc = stage_end(h, t_pair, h->side))) return rc;
     FCM_CUDA(cudaGetLastError());
     FCM_CUDA(cudaEventRecord(h->ev_join, h->side));
@@ -378,7 +417,7 @@ int run(fcm_handle* h, int n, const R* pos, const R* F, const R* T, R* U, R* W, 
     if (h->fp64)
       launch_spread_f64(h->gd, h->kd, torque, h->bb, n, (double*)h->grid, s, &h->launches);
     else
-      launch_spread_f32(h->gf, h->kf, torque, h->bb, (float*)h->grid, s, &h->launches);
+      launch_spread_f32(h->gf, h->kf, torque, h->p.spread_kernel, h->bb, (float*)h->grid, s, &h->launches);
     if ((rc = stage_end(h, t_spread, s))) return rc;
     FCM_CUDA(cudaGetLastError());
     if (!spread_only) {
@@ -440,6 +479,7 @@ int apply_common(fcm_handle* h, int n, const void* pos, const void* F, const voi
 
 }  // namespace
 
+#pragma GCC visibility push(default)
 extern "C" {
 
 int fcm_version(void) { return 10000; }
@@ -488,7 +528,8 @@ int fcm_create(const fcm_params* p, int device, fcm_handle** out) {
   fill_kernel_consts(h->p, SigmaD, &h->kd);
   make_pair_consts(p->a, p->eta, p->Sigma, SigmaD, pairs_on ? p->r_c : 0.0, 0.5 * sg, &h->pd);
   narrow_pair_consts(h->pd, &h->pf);
-  if (!h->fp64 && tile_smem_bytes(tile, p->M_G) > (size_t)tile_smem_limit()) {
+  if (!h->fp64 && (tile_smem_bytes(tile, p->M_G) > (size_t)tile_smem_limit() ||
+                   spread_smem_bytes(tile, p->M_G) > (size_t)tile_smem_limit())) {
     release(h);
     return fail(FCM_ERR_ARG, "M_G too large for the FP32 tile kernels");
   }
@@ -514,7 +555,23 @@ int fcm_create(const fcm_params* p, int device, fcm_handle** out) {
   h->grid_bytes = 3 * rsz * mtot;
   A(&h->grid, h->grid_bytes);
   A(&h->spec, 3 * 2 * rsz * ncplx);
+  void* table = nullptr;
+  if (!h->fp64 && pairs_on) A(&table, sizeof(float4) * 5 * kPairTableIntervals);
   if (rc != FCM_OK) { std::string e = g_error; release(h); return fail(rc, e); }
+  if (table) {
+    std::vector<float4> host(5 * kPairTableIntervals);
+    const double r_lo = 0.5 * sg;
+    const double r_hi = std::max(p->r_c, r_lo + 1e-3);  // below r_lo only the series is used
+    build_pair_table(h->pd, r_lo, r_hi, host.data());
+    if (cudaMemcpy(table, host.data(), sizeof(float4) * host.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+      release(h);
+      return fail(FCM_ERR_CUDA, "copy of the pair table failed");
+    }
+    h->ptab.coef = (const float4*)table;
+    h->ptab.r0 = (float)r_lo;
+    h->ptab.inv_h = (float)(kPairTableIntervals / (r_hi - r_lo));
+    h->ptab.n = kPairTableIntervals;
+  }
   cudaError_t ce = cudaMemset(b.tile_count, 0, 4 * (size_t)(b.ntiles + 1));
   if (ce == cudaSuccess) ce = cudaMemset(b.cell_count, 0, 4 * (size_t)(b.ncells + 1));
   if (ce == cudaSuccess) ce = cudaMemset(b.status, 0, 256);
@@ -673,3 +730,4 @@ int fcm_cutoff_radius(double Sigma, double Sigma_D, double a, double eta, double
 const char* fcm_last_error(void) { return g_error.c_str(); }
 
 }  // extern "C"
+#pragma GCC visibility pop

@@ -180,10 +180,42 @@ __host__ __device__ inline void pair_coeffs(R r2, const PairConsts<R>& C, R& al,
   dl = de * ir2;
 }
 
+// Piecewise-cubic tables of the five radial coefficients for the FP32 pair
+// kernel: interval i covers r in [r0 + i h, r0 + (i+1) h); coef[5 i + f] holds
+// (c0, c1, c2, c3) of function f (al, bt, cr, gm, dl) in u = (r - r0)/h - i.
+// Built on the host in FP64 from the closed form through four points per interval.
+constexpr int kPairTableIntervals = 1024;
+struct PairTable {
+  const float4* coef;
+  float r0, inv_h;
+  int n;
+};
+
+__device__ inline float cubic(float4 c, float u) { return fmaf(u, fmaf(u, fmaf(u, c.w, c.z), c.y), c.x); }
+
+__device__ inline void pair_coeffs_table(float r2, const PairConsts<float>& C, const PairTable& t, float& al,
+                                         float& bt, float& cr, float& gm, float& dl) {
+  if (r2 < C.rs2) {
+    pair_coeffs<float>(r2, C, al, bt, cr, gm, dl);
+    return;
+  }
+  float u = (sqrtf(r2) - t.r0) * t.inv_h;
+  int i = min(max((int)u, 0), t.n - 1);
+  u -= (float)i;
+  const float4* c = t.coef + 5 * i;
+  al = cubic(__ldg(c + 0), u);
+  bt = cubic(__ldg(c + 1), u);
+  cr = cubic(__ldg(c + 2), u);
+  gm = cubic(__ldg(c + 3), u);
+  dl = cubic(__ldg(c + 4), u);
+}
+
 // Host-side construction of the constants (double), then narrowing.
 void make_pair_consts(double a, double eta, double Sigma, double Sigma_D, double r_c,
                       double r_series, PairConsts<double>* out);
 void narrow_pair_consts(const PairConsts<double>& in, PairConsts<float>* out);
+// Fills host memory coef[5 * kPairTableIntervals] (float4 each) for r in [r_lo, r_hi].
+void build_pair_table(const PairConsts<double>& pd, double r_lo, double r_hi, float4* coef);
 
 // ---------------------------------------------------------------- launch API
 // Binning: wraps positions, computes tile and cell keys, counts and ranks,
@@ -205,15 +237,18 @@ void launch_binning(const Geometry<R>& g, int n, const R* pos, const R* F, const
 template <typename R>
 void launch_projection(const Geometry<R>& g, R eta, void* spectrum, cudaStream_t s, long long* launches);
 
-// FP32 tiled spread / gather (shared-memory tile accumulation, halo flush).
-size_t tile_smem_bytes(const int tile[3], int MG);
+// FP32 tiled spread / gather (tile accumulation, halo flush).
+size_t tile_smem_bytes(const int tile[3], int MG);      // extended region (gather, atomic spread)
+size_t spread_smem_bytes(const int tile[3], int MG);    // whichever spread kernel the tile selects
+bool spread_uses_rows(const int tile[3], int MG);       // row-stationary spread applies
 int tile_smem_limit();
-void launch_spread_f32(const Geometry<float>& g, const KernelConsts<float>& kc, bool torque,
+// spread_kernel: 0 = choose, 1 = row-stationary, 2 = shared atomics (fcm_params.spread_kernel).
+void launch_spread_f32(const Geometry<float>& g, const KernelConsts<float>& kc, bool torque, int spread_kernel,
                        const BinBuffers& b, float* grid, cudaStream_t s, long long* launches);
 void launch_gather_f32(const Geometry<float>& g, const KernelConsts<float>& kc, bool torque,
                        const BinBuffers& b, const float* grid, const float* upair, const float* wpair,
                        float* U, float* W, cudaStream_t s, long long* launches);
-void launch_pair_f32(const Geometry<float>& g, const PairConsts<float>& pc, bool torque,
+void launch_pair_f32(const Geometry<float>& g, const PairConsts<float>& pc, const PairTable& tab, bool torque,
                      const BinBuffers& b, int n, float* upair, float* wpair, cudaStream_t s,
                      long long* launches);
 

@@ -1,0 +1,169 @@
+// FP32 interpolation J~ + N~ on tiles (trapezoidal rule of Section 2.1 step 3,
+// eq. avg_particle_vel_mod and eq. avg_particle_rot_mod):
+//   U = h^3 sum_g u(x_g) Delta~(x_g - Y; Sigma)
+//   W = h^3 sum_g Delta(x_g - Y; Sigma_D) (d_g x u(x_g)) / (2 Sigma_D^2),  d_g = x_g - Y
+// (the second line is (1/2) int (curl u) Delta after one integration by parts,
+// the exact adjoint of the torque spread).
+//
+// One CTA per tile: the extended region of u is copied into shared memory with
+// asynchronous 4-byte copies (no register round trip), then a warp owns a
+// particle and its lanes own window rows; the M_G x-profiles are computed by
+// M_G lanes and broadcast into registers with warp shuffles. Per point: 3
+// shared loads and 8 FMA. The pair-correction sums, when present, are added
+// when U and W are written in input order.
+#include "grid_common.cuh"
+
+namespace fcm {
+
+__device__ inline void cp_async4(float* smem_dst, const float* gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+
+template <int MGT, bool GUARD, bool TORQUE, bool SAMEW>
+__global__ void __launch_bounds__(256) gather_tile_kernel(Geometry<float> g, KernelConsts<float> kc,
+                                                          const float4* __restrict__ pos,
+                                                          const int* __restrict__ tstart,
+                                                          const float* __restrict__ grid,
+                                                          const float* __restrict__ upair,
+                                                          const float* __restrict__ wpair,
+                                                          float* __restrict__ U, float* __restrict__ W) {
+  extern __shared__ float4 sm4[];
+  float* acc = reinterpret_cast<float*>(sm4);
+  const int t = blockIdx.x;
+  const int p0 = tstart[t], p1 = tstart[t + 1];
+  if (p0 >= p1) return;
+  const TileOrigin o = tile_origin(g, t);
+  const int MG = GUARD ? g.MG : MGT;
+  const ExtLayout l = ext_layout(g.tile, MG);
+  const size_t Mtot = (size_t)g.M[0] * g.M[1] * g.M[2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  {
+    const bool has_x = lane < l.EX;
+    const int gx = wrap_index(o.ox0 + lane, g.M[0]);
+    for (RowWalk rw = row_walk_begin(g, o, l); rw.r < rw.r1; row_walk_next(g, o, l, rw)) {
+      if (has_x)
+        cp_async4(acc + rw.c * l.C + rw.ez * l.Q + rw.ey * l.P + lane,
+                  grid + rw.c * Mtot + ((size_t)rw.gz * g.M[1] + rw.gy) * g.M[0] + gx);
+    }
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+  }
+  __syncthreads();
+
+  for (int p = p0 + warp; p < p1; p += nwarp) {
+    const float4 y = pos[p];
+    const int4 off = window_offset(g, o, y);
+    const float dxl = (float)(window_start(y.x, g.h[0], MG) + lane) * g.h[0] - y.x;
+    const float dyl = (float)(window_start(y.y, g.h[1], MG) + lane) * g.h[1] - y.y;
+    const float dzl = (float)(window_start(y.z, g.h[2], MG) + lane) * g.h[2] - y.z;
+    const float gxl = expf(-dxl * dxl * kc.inv2S2);
+    const float gyl = expf(-dyl * dyl * kc.inv2S2);
+    const float gzl = expf(-dzl * dzl * kc.inv2S2);
+    const float gdxl = SAMEW ? gxl : expf(-dxl * dxl * kc.inv2SD2);
+    const float gdyl = SAMEW ? gyl : expf(-dyl * dyl * kc.inv2SD2);
+    const float gdzl = SAMEW ? gzl : expf(-dzl * dzl * kc.inv2SD2);
+    float gx[MGT], gx2[MGT], gx1[MGT], gdx[MGT];
+#pragma unroll
+    for (int j = 0; j < MGT; ++j) {
+      const float gj = __shfl_sync(kFullMask32, gxl, j);
+      const float dj = __shfl_sync(kFullMask32, dxl, j);
+      const float gdj = SAMEW ? gj : __shfl_sync(kFullMask32, gdxl, j);
+      gx[j] = gj;
+      gx2[j] = dj * dj * gj;
+      gdx[j] = gdj;
+      gx1[j] = dj * gdj;
+    }
+    float u0 = 0.f, u1 = 0.f, u2 = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f;
+    int jy = lane, jz = 0;
+    while (jy >= MG) { jy -= MG; ++jz; }
+    for (int r0 = 0; r0 < MG * MG; r0 += 32) {
+      const bool active = r0 + lane < MG * MG;
+      const int sy = active ? jy : 0, sz = active ? jz : 0;
+      const float dy = __shfl_sync(kFullMask32, dyl, sy);
+      const float gy = __shfl_sync(kFullMask32, gyl, sy);
+      const float dz = __shfl_sync(kFullMask32, dzl, sz);
+      const float gz = __shfl_sync(kFullMask32, gzl, sz);
+      const float gdy = SAMEW ? gy : __shfl_sync(kFullMask32, gdyl, sy);
+      const float gdz = SAMEW ? gz : __shfl_sync(kFullMask32, gdzl, sz);
+      if (active) {
+        const float* row = acc + (off.z + jz) * l.Q + (off.y + jy) * l.P + off.x;
+        float sx0 = 0.f, sy0 = 0.f, sz0 = 0.f, sx2 = 0.f, sy2 = 0.f, sz2 = 0.f;
+        float dx0 = 0.f, dy0 = 0.f, dz0 = 0.f, dy1 = 0.f, dz1 = 0.f;
+#pragma unroll
+        for (int j = 0; j < MGT; ++j) {
+          if (!GUARD || j < MG) {
+            const float ux = row[j], uy = row[l.C + j], uz = row[2 * l.C + j];
+            sx0 = fmaf(gx[j], ux, sx0); sy0 = fmaf(gx[j], uy, sy0); sz0 = fmaf(gx[j], uz, sz0);
+            sx2 = fmaf(gx2[j], ux, sx2); sy2 = fmaf(gx2[j], uy, sy2); sz2 = fmaf(gx2[j], uz, sz2);
+            if (TORQUE) {
+              if (!SAMEW) { dx0 = fmaf(gdx[j], ux, dx0); dy0 = fmaf(gdx[j], uy, dy0); dz0 = fmaf(gdx[j], uz, dz0); }
+              dy1 = fmaf(gx1[j], uy, dy1);
+              dz1 = fmaf(gx1[j], uz, dz1);
+            }
+          }
+        }
+        const float G = kc.nrm * gy * gz;
+        const float GQ = G * fmaf(kc.B, fmaf(dy, dy, dz * dz), kc.A);
+        const float GB = G * kc.B;
+        u0 = fmaf(GQ, sx0, fmaf(GB, sx2, u0));
+        u1 = fmaf(GQ, sy0, fmaf(GB, sy2, u1));
+        u2 = fmaf(GQ, sz0, fmaf(GB, sz2, u2));
+        if (TORQUE) {
+          if (SAMEW) { dx0 = sx0; dy0 = sy0; dz0 = sz0; }
+          const float H = kc.tq * gdy * gdz;
+          w0 = fmaf(H, dy * dz0 - dz * dy0, w0);
+          w1 = fmaf(H, dz * dx0 - dz1, w1);
+          w2 = fmaf(H, dy1 - dy * dx0, w2);
+        }
+      }
+      jy += 32;
+      while (jy >= MG) { jy -= MG; ++jz; }
+    }
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+      u0 += __shfl_xor_sync(kFullMask32, u0, s);
+      u1 += __shfl_xor_sync(kFullMask32, u1, s);
+      u2 += __shfl_xor_sync(kFullMask32, u2, s);
+      if (TORQUE) {
+        w0 += __shfl_xor_sync(kFullMask32, w0, s);
+        w1 += __shfl_xor_sync(kFullMask32, w1, s);
+        w2 += __shfl_xor_sync(kFullMask32, w2, s);
+      }
+    }
+    if (lane == 0) {
+      const size_t oi = 3 * (size_t)index_from_w(y.w);
+      float a0 = kc.h3 * u0, a1 = kc.h3 * u1, a2 = kc.h3 * u2;
+      if (upair) { a0 += upair[oi]; a1 += upair[oi + 1]; a2 += upair[oi + 2]; }
+      U[oi] = a0; U[oi + 1] = a1; U[oi + 2] = a2;
+      if (TORQUE && W) {
+        float b0 = kc.h3 * w0, b1 = kc.h3 * w1, b2 = kc.h3 * w2;
+        if (wpair) { b0 += wpair[oi]; b1 += wpair[oi + 1]; b2 += wpair[oi + 2]; }
+        W[oi] = b0; W[oi + 1] = b1; W[oi + 2] = b2;
+      }
+    }
+  }
+}
+
+template <int MGT, bool GUARD, bool TORQUE, bool SAMEW>
+static void gather_variant(const Geometry<float>& g, const KernelConsts<float>& kc, const BinBuffers& b,
+                           const float* grid, const float* up, const float* wp, float* U, float* W,
+                           cudaStream_t s) {
+  const size_t smem = tile_smem_bytes(g.tile, g.MG);
+  auto k = gather_tile_kernel<MGT, GUARD, TORQUE, SAMEW>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k<<<b.ntiles, 256, smem, s>>>(g, kc, (const float4*)b.t_pos, b.tile_start, grid, up, wp, U, W);
+}
+
+void launch_gather_f32(const Geometry<float>& g, const KernelConsts<float>& kc, bool torque,
+                       const BinBuffers& b, const float* grid, const float* up, const float* wp,
+                       float* U, float* W, cudaStream_t s, long long* launches) {
+#define GATHER_CALL(MGT, GUARD)                                                                     \
+  if (!torque) gather_variant<MGT, GUARD, false, true>(g, kc, b, grid, up, wp, U, W, s);           \
+  else if (kc.same_width) gather_variant<MGT, GUARD, true, true>(g, kc, b, grid, up, wp, U, W, s); \
+  else gather_variant<MGT, GUARD, true, false>(g, kc, b, grid, up, wp, U, W, s);
+  FCM_DISPATCH_MG(g.MG, GATHER_CALL)
+#undef GATHER_CALL
+  *launches += 1;
+}
+
+}  // namespace fcm

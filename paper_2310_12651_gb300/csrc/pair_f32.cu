@@ -3,16 +3,17 @@
 // For particle n and every m with minimum-image r = |Y_n - Y_m| < r_c:
 //   U_n += al F_m + bt x (x.F_m) + cr (T_m x x)
 //   W_n += cr (F_m x x) + gm T_m + dl x (x.T_m)
-// with x = Y_n - Y_m and the radial coefficients of pair_coeffs (closed form in
-// FP32; Taylor series for r < r_series, which also covers coincident points),
-// plus the self correction. Candidates come from the 27 cells around n's cell
-// (Section 4 step 1); cells adjacent in x are contiguous in the cell-sorted
-// arrays, so a warp walks at most 9 ranges (more only where x wraps).
+// with x = Y_n - Y_m and the radial coefficients of the closed form, read from
+// piecewise-cubic tables built in FP64 (Taylor series for r < r_series, which
+// also covers coincident points), plus the self correction. Candidates come
+// from the 27 cells around n's cell (Section 4 step 1); cells adjacent in x are
+// contiguous in the cell-sorted arrays, so a warp walks at most 9 ranges (more
+// only where x wraps).
 //
 // GB300 decomposition: one warp per particle n. Lanes test 32 candidates at a
 // time; hits are compacted with a ballot into a per-warp shared-memory queue,
-// and the closed form runs when 32 hits are queued, so the transcendental work
-// runs with every lane busy although only ~15% of candidates are within r_c.
+// and the correction is evaluated when 32 hits are queued, so that work runs
+// with every lane busy although only ~15% of candidates are within r_c.
 // Per-lane sums are compensated (Neumaier); the warp reduction is a tree.
 #include "fcm_internal.cuh"
 
@@ -39,9 +40,10 @@ __device__ inline float min_image(float d, float L) {
 }
 
 template <bool TORQUE>
-__device__ inline void eval_pair(const PairConsts<float>& pc, float4 dq, float4 Fj, float4 Tj, Neu* u, Neu* w) {
+__device__ inline void eval_pair(const PairConsts<float>& pc, const PairTable& tab, float4 dq, float4 Fj, float4 Tj,
+                                 Neu* u, Neu* w) {
   float al, bt, cr, gm, dl;
-  pair_coeffs<float>(dq.w, pc, al, bt, cr, gm, dl);
+  pair_coeffs_table(dq.w, pc, tab, al, bt, cr, gm, dl);
   const float dx = dq.x, dy = dq.y, dz = dq.z;
   const float xF = dx * Fj.x + dy * Fj.y + dz * Fj.z;
   float u0 = al * Fj.x + bt * xF * dx;
@@ -64,7 +66,7 @@ __device__ inline void eval_pair(const PairConsts<float>& pc, float4 dq, float4 
 }
 
 template <bool TORQUE>
-__global__ void __launch_bounds__(kPairWarps * 32) pair_warp_kernel(Geometry<float> g, PairConsts<float> pc, int n,
+__global__ void __launch_bounds__(kPairWarps * 32) pair_warp_kernel(Geometry<float> g, PairConsts<float> pc, PairTable tab, int n,
                                                                     const float4* __restrict__ cpos,
                                                                     const float4* __restrict__ cF,
                                                                     const float4* __restrict__ cT,
@@ -125,7 +127,7 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_warp_kernel(Geometry<flo
             const float4 Fj = cF[jj];
             float4 Tj = make_float4(0.f, 0.f, 0.f, 0.f);
             if (TORQUE) Tj = cT[jj];
-            eval_pair<TORQUE>(pc, e, Fj, Tj, u, w);
+            eval_pair<TORQUE>(pc, tab, e, Fj, Tj, u, w);
             qh = (qh + 32) & (kQueue - 1);
             qn -= 32;
             __syncwarp();
@@ -141,7 +143,7 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_warp_kernel(Geometry<flo
     const float4 Fj = cF[jj];
     float4 Tj = make_float4(0.f, 0.f, 0.f, 0.f);
     if (TORQUE) Tj = cT[jj];
-    eval_pair<TORQUE>(pc, e, Fj, Tj, u, w);
+    eval_pair<TORQUE>(pc, tab, e, Fj, Tj, u, w);
   }
   float r[6] = {u[0].value(), u[1].value(), u[2].value(), w[0].value(), w[1].value(), w[2].value()};
 #pragma unroll
@@ -164,16 +166,16 @@ __global__ void __launch_bounds__(kPairWarps * 32) pair_warp_kernel(Geometry<flo
   }
 }
 
-void launch_pair_f32(const Geometry<float>& g, const PairConsts<float>& pc, bool torque, const BinBuffers& b,
-                     int n, float* upair, float* wpair, cudaStream_t s, long long* launches) {
+void launch_pair_f32(const Geometry<float>& g, const PairConsts<float>& pc, const PairTable& tab, bool torque,
+                     const BinBuffers& b, int n, float* upair, float* wpair, cudaStream_t s, long long* launches) {
   if (n <= 0) return;
   const int blocks = (n + kPairWarps - 1) / kPairWarps;
   if (torque)
-    pair_warp_kernel<true><<<blocks, kPairWarps * 32, 0, s>>>(g, pc, n, (const float4*)b.c_pos,
+    pair_warp_kernel<true><<<blocks, kPairWarps * 32, 0, s>>>(g, pc, tab, n, (const float4*)b.c_pos,
                                                               (const float4*)b.c_F, (const float4*)b.c_T,
                                                               b.cell_start, upair, wpair);
   else
-    pair_warp_kernel<false><<<blocks, kPairWarps * 32, 0, s>>>(g, pc, n, (const float4*)b.c_pos,
+    pair_warp_kernel<false><<<blocks, kPairWarps * 32, 0, s>>>(g, pc, tab, n, (const float4*)b.c_pos,
                                                                (const float4*)b.c_F, (const float4*)b.c_T,
                                                                b.cell_start, upair, wpair);
   *launches += 1;

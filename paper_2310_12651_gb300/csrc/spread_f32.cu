@@ -1,0 +1,366 @@
+// FP32 spread J~^dagger + N~^dagger on tiles (Section 3.1, Section 3.4):
+//   f(x_g) += F Delta~(x_g - Y; Sigma) - (1/2) T x grad Delta(x_g - Y; Sigma_D)
+// with Delta~ = Delta(.; Sigma) (A + B |d|^2), A = 1 - 3 dd/(2 Sigma^2),
+// B = dd/(2 Sigma^4), over each particle's M_G^3 window.
+//
+// spread_rows_kernel (default, M_G <= 16): every thread owns one (y, z) row of
+// the tile's extended region and keeps its EX x 3 sums in registers. All
+// threads walk the tile's particles together; each particle's x/y/z profiles
+// are staged once in shared memory and read as broadcasts. No two threads add
+// to the same point, so there are no atomics and the order of the sum over
+// particles is fixed. At the end each thread adds its row to the grid with
+// 16-byte global reductions (the halo flush).
+//
+// spread_tile_kernel (any M_G): warp per particle, lanes on window rows, shared
+// memory atomics into the extended region (bank-conflict-free layout), then
+// the same flush from shared memory with coalesced reductions.
+#include "grid_common.cuh"
+
+namespace fcm {
+
+template <int OX, int MGT, int EXT, bool GUARD, bool TORQUE, bool SAMEW>
+__device__ __forceinline__ void add_row(const float4* __restrict__ xt, int MG, float (&sx)[EXT], float (&sy)[EXT],
+                                        float (&sz)[EXT], float ax, float ay, float az, float bx, float by, float bz,
+                                        float cx, float cy, float cz, float ky, float kz) {
+#pragma unroll
+  for (int j = 0; j < MGT; ++j) {
+    if (!GUARD || j < MG) {
+      const float4 xv = xt[j];
+      float vx = fmaf(bx, xv.y, fmaf(ax, xv.x, sx[OX + j]));
+      float vy = fmaf(by, xv.y, fmaf(ay, xv.x, sy[OX + j]));
+      float vz = fmaf(bz, xv.y, fmaf(az, xv.x, sz[OX + j]));
+      if (TORQUE) {
+        vy = fmaf(ky, xv.z, vy);
+        vz = fmaf(kz, xv.z, vz);
+        if (!SAMEW) {
+          vx = fmaf(cx, xv.w, vx);
+          vy = fmaf(cy, xv.w, vy);
+          vz = fmaf(cz, xv.w, vz);
+        }
+      }
+      sx[OX + j] = vx;
+      sy[OX + j] = vy;
+      sz[OX + j] = vz;
+    }
+  }
+}
+
+template <int EXT, bool GUARD>
+__device__ __forceinline__ void flush_row(const Geometry<float>& g, const TileOrigin& o, int EX, float* __restrict__ row,
+                                          const float (&s)[EXT]) {
+  const bool vec = (o.ox0 + EX <= g.M[0]) && ((g.M[0] & 3) == 0);
+  if (vec) {
+    float* p = row + o.ox0;
+#pragma unroll
+    for (int k = 0; k + 3 < EXT; k += 4) {
+      if (!GUARD || k + 3 < EX) {
+        if (s[k] != 0.f || s[k + 1] != 0.f || s[k + 2] != 0.f || s[k + 3] != 0.f)
+          red_add_v4(p + k, s[k], s[k + 1], s[k + 2], s[k + 3]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (k + e < EX && s[k + e] != 0.f) atomicAdd(p + k + e, s[k + e]);
+      }
+    }
+#pragma unroll
+    for (int k = (EXT / 4) * 4; k < EXT; ++k)
+      if ((!GUARD || k < EX) && s[k] != 0.f) atomicAdd(p + k, s[k]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < EXT; ++k)
+      if ((!GUARD || k < EX) && s[k] != 0.f) atomicAdd(row + wrap_index(o.ox0 + k, g.M[0]), s[k]);
+  }
+}
+
+// Threads of the rows kernel: one per extended (y, z) row, at most (7 + M_G)^2
+// with an 8-point tile (M_G = 16 uses a 4-point tile in y and z).
+constexpr int rows_threads(int MGT) {
+  return MGT <= 14 ? (((7 + MGT) * (7 + MGT) + 31) / 32) * 32 : kRowsMaxThreads;
+}
+
+template <int MGT, bool GUARD, bool TORQUE, bool SAMEW>
+__global__ void __launch_bounds__(rows_threads(MGT), 1) spread_rows_kernel(Geometry<float> g, KernelConsts<float> kc,
+                                                                        const float4* __restrict__ pos,
+                                                                        const float4* __restrict__ Fv,
+                                                                        const float4* __restrict__ Tv,
+                                                                        const int* __restrict__ tstart,
+                                                                        float* __restrict__ grid) {
+  constexpr int TX = 8;
+  constexpr int EXT = TX + MGT - 1;
+  extern __shared__ float4 sm4[];
+  const int t = blockIdx.x;
+  const int p0 = tstart[t], p1 = tstart[t + 1];
+  if (p0 >= p1) return;
+  const TileOrigin o = tile_origin(g, t);
+  const int MG = GUARD ? g.MG : MGT;
+  const int EY = g.tile[1] + MG - 1, EZ = g.tile[2] + MG - 1;
+  const int R = EY * EZ;
+  const int row = threadIdx.x;
+  const bool has_row = row < R;
+  const int ez = has_row ? row / EY : 0;
+  const int ey = has_row ? row - ez * EY : 0;
+  float sx[EXT], sy[EXT], sz[EXT];
+#pragma unroll
+  for (int k = 0; k < EXT; ++k) { sx[k] = 0.f; sy[k] = 0.f; sz[k] = 0.f; }
+  const RowTables tb = row_tables<MGT>(sm4);
+
+  for (int base = p0; base < p1; base += kRowsChunk) {
+    const int np = min(kRowsChunk, p1 - base);
+    __syncthreads();
+    for (int k = threadIdx.x; k < np * 3 * MGT; k += blockDim.x) {
+      const int q = k / (3 * MGT);
+      const int rem = k - q * 3 * MGT;
+      const int d = rem / MGT;
+      const int j = rem - d * MGT;
+      const float4 y = pos[base + q];
+      const float yd = d == 0 ? y.x : (d == 1 ? y.y : y.z);
+      const float h = g.h[d];
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (j < MG) {
+        const float dd = (float)(window_start(yd, h, MG) + j) * h - yd;
+        const float gs = expf(-dd * dd * kc.inv2S2);
+        const float gd = SAMEW ? gs : expf(-dd * dd * kc.inv2SD2);
+        v = (d == 0) ? make_float4(gs, dd * dd * gs, dd * gd, gd) : make_float4(gs, dd, gd, 0.f);
+      }
+      (d == 0 ? tb.xt : (d == 1 ? tb.yt : tb.zt))[q * MGT + j] = v;
+    }
+    for (int q = threadIdx.x; q < np; q += blockDim.x) {
+      tb.po[q] = window_offset(g, o, pos[base + q]);
+      tb.pf[q] = Fv[base + q];
+      tb.pt[q] = TORQUE ? Tv[base + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    if (!has_row) continue;
+    for (int q = 0; q < np; ++q) {
+      const int4 off = tb.po[q];
+      const int jy = ey - off.y, jz = ez - off.z;
+      if ((unsigned)jy >= (unsigned)MG || (unsigned)jz >= (unsigned)MG) continue;
+      const float4 yv = tb.yt[q * MGT + jy];
+      const float4 zv = tb.zt[q * MGT + jz];
+      const float4 f = tb.pf[q];
+      const float G = kc.nrm * yv.x * zv.x;
+      const float GQ = G * fmaf(kc.B, fmaf(yv.y, yv.y, zv.y * zv.y), kc.A);
+      const float GB = G * kc.B;
+      float ax = f.x * GQ, ay = f.y * GQ, az = f.z * GQ;
+      const float bx = f.x * GB, by = f.y * GB, bz = f.z * GB;
+      float cx = 0.f, cy = 0.f, cz = 0.f, ky = 0.f, kz = 0.f;
+      if (TORQUE) {
+        const float4 tq = tb.pt[q];
+        const float H = kc.tq * yv.z * zv.z;
+        const float dy = yv.y, dz = zv.y;
+        cx = H * (tq.y * dz - tq.z * dy);
+        cy = -H * tq.x * dz;
+        cz = H * tq.x * dy;
+        ky = H * tq.z;
+        kz = -H * tq.y;
+        if (SAMEW) { ax += cx; ay += cy; az += cz; }
+      }
+      const float4* xt = tb.xt + q * MGT;
+#define FCM_ROW_CASE(OX)                                                                                     \
+  case OX:                                                                                                   \
+    add_row<OX, MGT, EXT, GUARD, TORQUE, SAMEW>(xt, MG, sx, sy, sz, ax, ay, az, bx, by, bz, cx, cy, cz, ky, kz); \
+    break;
+      switch (off.x) {
+        FCM_ROW_CASE(0) FCM_ROW_CASE(1) FCM_ROW_CASE(2) FCM_ROW_CASE(3)
+        FCM_ROW_CASE(4) FCM_ROW_CASE(5) FCM_ROW_CASE(6) FCM_ROW_CASE(7)
+        default: break;
+      }
+#undef FCM_ROW_CASE
+    }
+  }
+  if (has_row) {
+    const size_t Mtot = (size_t)g.M[0] * g.M[1] * g.M[2];
+    const int gy = wrap_index(o.oy0 + ey, g.M[1]);
+    const int gz = wrap_index(o.oz0 + ez, g.M[2]);
+    float* r0 = grid + ((size_t)gz * g.M[1] + gy) * g.M[0];
+    const int EX = TX + MG - 1;
+    flush_row<EXT, GUARD>(g, o, EX, r0, sx);
+    flush_row<EXT, GUARD>(g, o, EX, r0 + Mtot, sy);
+    flush_row<EXT, GUARD>(g, o, EX, r0 + 2 * Mtot, sz);
+  }
+}
+
+// ---------------------------------------------------------------- atomic kernel
+
+template <int MGT, bool GUARD, bool TORQUE, bool SAMEW>
+__global__ void __launch_bounds__(256) spread_tile_kernel(Geometry<float> g, KernelConsts<float> kc,
+                                                          const float4* __restrict__ pos,
+                                                          const float4* __restrict__ Fv,
+                                                          const float4* __restrict__ Tv,
+                                                          const int* __restrict__ tstart,
+                                                          float* __restrict__ grid) {
+  extern __shared__ float4 sm4[];
+  float* acc = reinterpret_cast<float*>(sm4);
+  const int t = blockIdx.x;
+  const int p0 = tstart[t], p1 = tstart[t + 1];
+  if (p0 >= p1) return;
+  const TileOrigin o = tile_origin(g, t);
+  const int MG = GUARD ? g.MG : MGT;
+  const ExtLayout l = ext_layout(g.tile, MG);
+  for (int k = threadIdx.x; k < 3 * l.C; k += blockDim.x) acc[k] = 0.f;
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int p = p0 + warp; p < p1; p += nwarp) {
+    const float4 y = pos[p];
+    const float4 f = Fv[p];
+    float4 tq = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (TORQUE) tq = Tv[p];
+    const int4 off = window_offset(g, o, y);
+    // lane l < MG holds the l-th point of each axis
+    const float dxl = (float)(window_start(y.x, g.h[0], MG) + lane) * g.h[0] - y.x;
+    const float dyl = (float)(window_start(y.y, g.h[1], MG) + lane) * g.h[1] - y.y;
+    const float dzl = (float)(window_start(y.z, g.h[2], MG) + lane) * g.h[2] - y.z;
+    const float gxl = expf(-dxl * dxl * kc.inv2S2);
+    const float gyl = expf(-dyl * dyl * kc.inv2S2);
+    const float gzl = expf(-dzl * dzl * kc.inv2S2);
+    const float gdxl = SAMEW ? gxl : expf(-dxl * dxl * kc.inv2SD2);
+    const float gdyl = SAMEW ? gyl : expf(-dyl * dyl * kc.inv2SD2);
+    const float gdzl = SAMEW ? gzl : expf(-dzl * dzl * kc.inv2SD2);
+    float gx[MGT], gx2[MGT], gx1[MGT], gdx[MGT];
+#pragma unroll
+    for (int j = 0; j < MGT; ++j) {
+      const float gj = __shfl_sync(kFullMask32, gxl, j);
+      const float dj = __shfl_sync(kFullMask32, dxl, j);
+      const float gdj = SAMEW ? gj : __shfl_sync(kFullMask32, gdxl, j);
+      gx[j] = gj;
+      gx2[j] = dj * dj * gj;
+      gdx[j] = gdj;
+      gx1[j] = dj * gdj;
+    }
+    int jy = lane, jz = 0;
+    while (jy >= MG) { jy -= MG; ++jz; }
+    for (int r0 = 0; r0 < MG * MG; r0 += 32) {
+      const bool active = r0 + lane < MG * MG;
+      const int sy = active ? jy : 0, sz = active ? jz : 0;
+      const float dy = __shfl_sync(kFullMask32, dyl, sy);
+      const float gy = __shfl_sync(kFullMask32, gyl, sy);
+      const float dz = __shfl_sync(kFullMask32, dzl, sz);
+      const float gz = __shfl_sync(kFullMask32, gzl, sz);
+      const float gdy = SAMEW ? gy : __shfl_sync(kFullMask32, gdyl, sy);
+      const float gdz = SAMEW ? gz : __shfl_sync(kFullMask32, gdzl, sz);
+      if (active) {
+        const float G = kc.nrm * gy * gz;
+        const float GQ = G * fmaf(kc.B, fmaf(dy, dy, dz * dz), kc.A);
+        const float GB = G * kc.B;
+        float ax = f.x * GQ, ay = f.y * GQ, az = f.z * GQ;
+        const float bx = f.x * GB, by = f.y * GB, bz = f.z * GB;
+        float* rowp = acc + (off.z + jz) * l.Q + (off.y + jy) * l.P + off.x;
+        float cx = 0.f, cy = 0.f, cz = 0.f, ky = 0.f, kz = 0.f;
+        if (TORQUE) {
+          const float H = kc.tq * gdy * gdz;
+          cx = H * (tq.y * dz - tq.z * dy);
+          cy = -H * tq.x * dz;
+          cz = H * tq.x * dy;
+          ky = H * tq.z;
+          kz = -H * tq.y;
+          if (SAMEW) { ax += cx; ay += cy; az += cz; }
+        }
+#pragma unroll
+        for (int j = 0; j < MGT; ++j) {
+          if (!GUARD || j < MG) {
+            float vx = fmaf(bx, gx2[j], ax * gx[j]);
+            float vy = fmaf(by, gx2[j], ay * gx[j]);
+            float vz = fmaf(bz, gx2[j], az * gx[j]);
+            if (TORQUE) {
+              vy = fmaf(ky, gx1[j], vy);
+              vz = fmaf(kz, gx1[j], vz);
+              if (!SAMEW) { vx = fmaf(cx, gdx[j], vx); vy = fmaf(cy, gdx[j], vy); vz = fmaf(cz, gdx[j], vz); }
+            }
+            atomicAdd(rowp + j, vx);
+            atomicAdd(rowp + l.C + j, vy);
+            atomicAdd(rowp + 2 * l.C + j, vz);
+          }
+        }
+      }
+      jy += 32;
+      while (jy >= MG) { jy -= MG; ++jz; }
+    }
+  }
+  __syncthreads();
+  const size_t Mtot = (size_t)g.M[0] * g.M[1] * g.M[2];
+  const bool has_x = lane < l.EX;
+  const int gxw = wrap_index(o.ox0 + lane, g.M[0]);
+  for (RowWalk w = row_walk_begin(g, o, l); w.r < w.r1; row_walk_next(g, o, l, w)) {
+    if (!has_x) continue;
+    const float v = acc[w.c * l.C + w.ez * l.Q + w.ey * l.P + lane];
+    if (v != 0.f) atomicAdd(grid + w.c * Mtot + ((size_t)w.gz * g.M[1] + w.gy) * g.M[0] + gxw, v);
+  }
+}
+
+// ---------------------------------------------------------------- sizing and launch
+
+size_t tile_smem_bytes(const int tile[3], int MG) {
+  const ExtLayout l = ext_layout(tile, MG);
+  return sizeof(float) * 3 * (size_t)l.C;
+}
+
+int tile_smem_limit() { return 227 * 1024; }
+
+static int rows_mgt(int MG) {
+  switch (MG) {
+    case 10: case 12: case 14: case 16: return MG;
+    default: return MG <= 8 ? 8 : (MG <= 12 ? 12 : (MG <= 16 ? 16 : 0));
+  }
+}
+
+bool spread_uses_rows(const int tile[3], int MG) {
+  const int mgt = rows_mgt(MG);
+  if (tile[0] != 8 || mgt == 0) return false;
+  return (tile[1] + MG - 1) * (tile[2] + MG - 1) <= rows_threads(mgt);
+}
+
+static bool rows_selected(const Geometry<float>& g, int spread_kernel) {
+  if (spread_kernel == 2) return false;
+  return spread_uses_rows(g.tile, g.MG);
+}
+
+size_t spread_smem_bytes(const int tile[3], int MG) {
+  if (!spread_uses_rows(tile, MG)) return tile_smem_bytes(tile, MG);
+  const size_t tab = row_tables_bytes(rows_mgt(MG));
+  const size_t ext = tile_smem_bytes(tile, MG);
+  return tab > ext ? tab : ext;  // either kernel may be selected for this tile
+}
+
+template <int MGT, bool GUARD, bool TORQUE, bool SAMEW>
+static void rows_variant(const Geometry<float>& g, const KernelConsts<float>& kc, const BinBuffers& b, float* grid,
+                         cudaStream_t s) {
+  const size_t smem = row_tables_bytes(MGT);
+  const int threads = (((g.tile[1] + g.MG - 1) * (g.tile[2] + g.MG - 1) + 31) / 32) * 32;
+  auto k = spread_rows_kernel<MGT, GUARD, TORQUE, SAMEW>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k<<<b.ntiles, threads, smem, s>>>(g, kc, (const float4*)b.t_pos, (const float4*)b.t_F, (const float4*)b.t_T,
+                                    b.tile_start, grid);
+}
+
+template <int MGT, bool GUARD, bool TORQUE, bool SAMEW>
+static void atomic_variant(const Geometry<float>& g, const KernelConsts<float>& kc, const BinBuffers& b,
+                           float* grid, cudaStream_t s) {
+  const size_t smem = tile_smem_bytes(g.tile, g.MG);
+  auto k = spread_tile_kernel<MGT, GUARD, TORQUE, SAMEW>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k<<<b.ntiles, 256, smem, s>>>(g, kc, (const float4*)b.t_pos, (const float4*)b.t_F, (const float4*)b.t_T,
+                                b.tile_start, grid);
+}
+
+void launch_spread_f32(const Geometry<float>& g, const KernelConsts<float>& kc, bool torque, int spread_kernel,
+                       const BinBuffers& b, float* grid, cudaStream_t s, long long* launches) {
+  if (rows_selected(g, spread_kernel)) {
+#define ROWS_CALL(MGT, GUARD)                                                              \
+  if (!torque) rows_variant<MGT, GUARD, false, true>(g, kc, b, grid, s);                  \
+  else if (kc.same_width) rows_variant<MGT, GUARD, true, true>(g, kc, b, grid, s);        \
+  else rows_variant<MGT, GUARD, true, false>(g, kc, b, grid, s);
+    FCM_DISPATCH_ROWS(g.MG, ROWS_CALL)
+#undef ROWS_CALL
+  } else {
+#define ATOMIC_CALL(MGT, GUARD)                                                            \
+  if (!torque) atomic_variant<MGT, GUARD, false, true>(g, kc, b, grid, s);                \
+  else if (kc.same_width) atomic_variant<MGT, GUARD, true, true>(g, kc, b, grid, s);      \
+  else atomic_variant<MGT, GUARD, true, false>(g, kc, b, grid, s);
+    FCM_DISPATCH_MG(g.MG, ATOMIC_CALL)
+#undef ATOMIC_CALL
+  }
+  *launches += 1;
+}
+
+}  // namespace fcm

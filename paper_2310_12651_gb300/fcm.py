@@ -40,6 +40,7 @@ class Params(ctypes.Structure):
         ("precision", ctypes.c_int),
         ("max_n", ctypes.c_int),
         ("tile", ctypes.c_int * 3),
+        ("spread_kernel", ctypes.c_int),
     ]
 
 
@@ -93,7 +94,8 @@ def version() -> int:
     return _lib.fcm_version()
 
 
-def make_params(L, M, Sigma, r_c, M_G, max_n, precision=FCM_FP32, a=1.0, eta=1.0, Sigma_D=0.0, tile=(0, 0, 0)):
+def make_params(L, M, Sigma, r_c, M_G, max_n, precision=FCM_FP32, a=1.0, eta=1.0, Sigma_D=0.0, tile=(0, 0, 0),
+                spread_kernel=0):
     p = Params()
     _check(_lib.fcm_params_default(ctypes.byref(p)))
     Ls = [float(L)] * 3 if not hasattr(L, "__len__") else [float(v) for v in L]
@@ -104,6 +106,7 @@ def make_params(L, M, Sigma, r_c, M_G, max_n, precision=FCM_FP32, a=1.0, eta=1.0
         p.tile[k] = int(tile[k])
     p.a, p.eta, p.Sigma, p.Sigma_D, p.r_c = float(a), float(eta), float(Sigma), float(Sigma_D), float(r_c)
     p.M_G, p.precision, p.max_n = int(M_G), int(precision), int(max_n)
+    p.spread_kernel = int(spread_kernel)
     return p
 
 

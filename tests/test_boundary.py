@@ -40,7 +40,7 @@ def test_params_struct_matches_header(fcm):
     body = re.search(r"typedef struct fcm_params \{(.*?)\} fcm_params;", text, re.S).group(1)
     fields = re.findall(r"^\s*(?:double|int)\s+(\w+)", body, re.M)
     assert fields == [f[0] for f in fcm.Params._fields_]
-    assert ctypes.sizeof(fcm.Params) == 3 * 8 + 3 * 4 + 4 + 5 * 8 + 3 * 4 + 3 * 4
+    assert ctypes.sizeof(fcm.Params) == 3 * 8 + 3 * 4 + 4 + 5 * 8 + 3 * 4 + 3 * 4 + 4 + 4
 
 
 @pytest.mark.parametrize("change, message", [

@@ -59,6 +59,19 @@ def test_fp32_torques_several_tiles(fcm, Sigma, M):
     assert_parity(W, Wo, FP32_TOL, f"W fp32 Sigma={Sigma}")
 
 
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_fp32_both_spread_kernels(fcm, kernel):
+    """Row-stationary (1) and shared-atomic (2) spread kernels give the same product."""
+    torch = torch_cuda()
+    s = suspension(5000, 0.05, 48, 2.0, 1e-6, 66)
+    p = fcm.make_params(s.L, s.M, s.Sigma, s.r_c, s.M_G, s.n, fcm.FCM_FP32, spread_kernel=kernel)
+    with fcm.Handle(p) as h:
+        U, W = run_gpu(s, fcm.FCM_FP32, handle=h)
+    Uo, Wo = s.oracle(fcm.FCM_FP32)
+    assert_parity(U, Uo, FP32_TOL, f"U spread kernel {kernel}")
+    assert_parity(W, Wo, FP32_TOL, f"W spread kernel {kernel}")
+
+
 def test_fp32_forces_only(fcm):
     s = suspension(4000, 0.05, 40, 2.0, 1e-6, 44, torques=False)
     U, _ = run_gpu(s, fcm.FCM_FP32, want_W=False)
