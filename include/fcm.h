@@ -157,6 +157,30 @@ size_t fcm_workspace_bytes(const fcm_handle* h);
 int fcm_cutoff_radius(double Sigma, double Sigma_D, double a, double eta, double tol,
                       int torques, double* r_c);
 
+/* Capacity of fcm_pair_correction_noalloc's fixed scratch. */
+#define FCM_NOALLOC_MAX_N 65536
+#define FCM_NOALLOC_MAX_CELLS 65536
+
+/* The pairwise and self corrections (M - M~)(F, T) of one FP32 system, like
+ * fcm_apply_stages(..., FCM_STAGE_PAIR), for callers that cannot allocate
+ * device memory (an allocator or arena that owns the device, code running
+ * while a graph is captured, hosts that forbid cudaMalloc after start-up).
+ * The paper has no counterpart: this entry point exists for those callers.
+ *   p      : L, a, eta, Sigma, Sigma_D, r_c of the system (precision must be
+ *            FCM_FP32; M, M_G, max_n and tile are not used)
+ *   n      : 0 <= n <= FCM_NOALLOC_MAX_N; the pair cells, max(int(L_i/r_c), 3)
+ *            per dimension, must number at most FCM_NOALLOC_MAX_CELLS
+ *   pos, F, T (T may be NULL), U, W (W may be NULL): as for fcm_apply, on the
+ *            current CUDA device
+ * It allocates nothing: all scratch (about 7.7 MB) is one fixed file-scope
+ * device array, held by every GPU that loads the library until the process
+ * exits. The first call on a device looks up that array's address with the
+ * device current; make it before any stream capture. Every call shares the
+ * array and clears its counters first; calls whose work overlaps on the GPU
+ * race on it. Sizes beyond the limits return FCM_ERR_ARG with a message. */
+int fcm_pair_correction_noalloc(const fcm_params* p, int n, const void* pos, const void* F, const void* T,
+                                void* U, void* W, void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* fcm_last_error(void);
 

@@ -164,6 +164,8 @@ void narrow_pair_consts(const PairConsts<double>& in, PairConsts<float>* o) {
   for (size_t k = 0; k < sizeof(PairConsts<float>) / sizeof(float); ++k) dst[k] = (float)src[k];
 }
 
+int record_error(int code, const char* msg) { return fail(code, msg); }
+
 void build_pair_table(const PairConsts<double>& pd, double r_lo, double r_hi, float4* coef) {
   PairConsts<double> c = pd;
   c.rs2 = 0.0;  // the closed form throughout the tabulated range

@@ -262,6 +262,9 @@ void launch_pair_f64(const Geometry<double>& g, const PairConsts<double>& pc, bo
                      const BinBuffers& b, int n, double* upair, double* wpair, cudaStream_t s,
                      long long* launches);
 
+// Sets the message fcm_last_error() returns on this thread; returns code.
+int record_error(int code, const char* msg);
+
 // Zero-fill of a device range (a kernel of this library, counted as a launch).
 void launch_zero(void* p, size_t bytes, cudaStream_t s, long long* launches);
 

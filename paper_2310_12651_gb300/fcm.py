@@ -64,6 +64,7 @@ def _load():
         "fcm_launch_count": (ll, [vp]),
         "fcm_workspace_bytes": (sz, [vp]),
         "fcm_cutoff_radius": (i, [d, d, d, d, d, i, ctypes.POINTER(d)]),
+        "fcm_pair_correction_noalloc": (i, [ctypes.POINTER(Params), i, vp, vp, vp, vp, vp, vp]),
         "fcm_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -78,7 +79,11 @@ _lib = _load()
 #: symbols declared in include/fcm.h, for the export check
 EXPORTED = ("fcm_version", "fcm_params_default", "fcm_create", "fcm_destroy", "fcm_apply", "fcm_apply_stages",
             "fcm_spread", "fcm_copy_grid", "fcm_check", "fcm_set_timing", "fcm_read_timing", "fcm_launch_count",
-            "fcm_workspace_bytes", "fcm_cutoff_radius", "fcm_last_error")
+            "fcm_workspace_bytes", "fcm_cutoff_radius", "fcm_pair_correction_noalloc", "fcm_last_error")
+
+#: capacity of fcm_pair_correction_noalloc's fixed scratch (include/fcm.h)
+NOALLOC_MAX_N = 65536
+NOALLOC_MAX_CELLS = 65536
 
 
 def library():
@@ -189,6 +194,12 @@ class Handle:
 
     def workspace_bytes(self) -> int:
         return int(_lib.fcm_workspace_bytes(self._h))
+
+
+def pair_correction_noalloc(params: Params, n, pos, F, T, U, W, stream=0):
+    """(M - M~)(F, T) through the entry point that allocates no device memory."""
+    _check(_lib.fcm_pair_correction_noalloc(ctypes.byref(params), int(n), _ptr(pos), _ptr(F), _ptr(T), _ptr(U),
+                                            _ptr(W), stream or None))
 
 
 # ---- torch helpers (memory and streams only) ------------------------------------
