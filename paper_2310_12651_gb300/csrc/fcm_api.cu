@@ -305,8 +305,9 @@ void fill_geometry(const fcm_params& p, const int tile[3], Geometry<R>* g) {
     g->M[d] = p.M[d];
     g->tile[d] = tile[d];
     g->ntile[d] = (p.M[d] + tile[d] - 1) / tile[d];
-    int m = (p.r_c > 0) ? (int)(p.L[d] / p.r_c) : 3;
-    g->mcell[d] = std::max(m, 3);
+    // cells per dimension max(int(L/r_c), 3), clamped before the integer conversion
+    const double m = (p.r_c > 0) ? std::floor(p.L[d] / p.r_c) : 3.0;
+    g->mcell[d] = (int)std::min(std::max(m, 3.0), 1048576.0);
     g->cellw_inv[d] = (R)(g->mcell[d] / p.L[d]);
   }
   g->MG = p.M_G;
@@ -544,8 +545,12 @@ int fcm_create(const fcm_params* p, int device, fcm_handle** out) {
   const size_t ncplx = (size_t)(p->M[0] / 2 + 1) * p->M[1] * p->M[2];
   BinBuffers& b = h->bb;
   b.ntiles = h->gf.ntile[0] * h->gf.ntile[1] * h->gf.ntile[2];
-  b.ncells = pairs_on ? h->gf.mcell[0] * h->gf.mcell[1] * h->gf.mcell[2] : 1;
-  if ((size_t)b.ncells > (1u << 26)) { release(h); return fail(FCM_ERR_ARG, "too many pair cells (r_c too small for L)"); }
+  const double ncells_d = (double)h->gf.mcell[0] * h->gf.mcell[1] * h->gf.mcell[2];
+  if (pairs_on && ncells_d > (double)(1u << 26)) {
+    release(h);
+    return fail(FCM_ERR_ARG, "too many pair cells (r_c too small for L)");
+  }
+  b.ncells = pairs_on ? (int)ncells_d : 1;
   A((void**)&b.tile_key, 4 * n); A((void**)&b.tile_rank, 4 * n);
   A((void**)&b.cell_key, 4 * n); A((void**)&b.cell_rank, 4 * n);
   A((void**)&b.tile_count, 4 * (size_t)(b.ntiles + 1)); A((void**)&b.tile_start, 4 * (size_t)(b.ntiles + 1));

@@ -53,6 +53,7 @@ def test_params_struct_matches_header(fcm):
     (dict(L=float("nan")), "L must"),
     (dict(precision=7), "precision"),
     (dict(Sigma_D=0.1), "Sigma_D"),
+    (dict(r_c=1e-9), "pair cells"),
 ])
 def test_invalid_parameters_are_rejected_on_the_host(fcm, change, message):
     kw = dict(L=100.0, M=64, Sigma=2.0, r_c=16.9, M_G=12, max_n=10)
