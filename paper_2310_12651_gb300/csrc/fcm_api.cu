@@ -1,12 +1,14 @@
 // libfcm C-ABI: handle lifetime, parameter checks, workspace, and the launch
 // sequence of one mobility product (Section 4):
 //
-//   caller stream : bin ──► zero grid ─► spread ─► R2C ─► project ─► C2R ─┐
-//                     └─(event)─► side stream: pair correction ──(event)─┴► gather (+ pair sums) ─► U, W
+//   caller stream : bin ─► zero grid ─► spread ─┬─► R2C ─► project ─► C2R ─┐
+//                                               └─(event)─► side: pair ─(event)─┴► gather (+ pair sums) ─► U, W
 //
-// The pair correction only needs the cell-sorted particles, so it runs on the
-// handle's side stream while the grid stages run; the gather kernel adds the
-// pair sums when it writes U and W in input order. The fork/join uses events
+// The pair correction only needs the cell-sorted particles. It is forked onto
+// the handle's side stream after the spread, where it overlaps the
+// latency-bound FFT chain (spread and pair both fill the GPU, so overlapping
+// them gains nothing); the gather kernel adds the pair sums when it writes U
+// and W in input order. The fork/join uses events
 // only, so a caller may capture fcm_apply into a CUDA graph.
 #include <cufft.h>
 
@@ -386,6 +388,26 @@ int stage_end(fcm_handle* h, int slot, cudaStream_t s) {
   return FCM_OK;
 }
 
+// Forks the pair correction onto the side stream (it needs only the cell-sorted
+// particles); the caller joins on ev_join before the gather.
+template <typename R>
+int launch_pair_stage(fcm_handle* h, int n, R* U, R* Wout, bool torque, bool grid_on, cudaStream_t s) {
+  int rc, t_pair;
+  R* up = grid_on ? (R*)h->upair : U;
+  R* wp = grid_on ? (R*)h->wpair : Wout;
+  FCM_CUDA(cudaEventRecord(h->ev_fork, s));
+  FCM_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+  if ((rc = stage_begin(h, 4, h->side, &t_pair))) return rc;
+  if (h->fp64)
+    launch_pair_f64(h->gd, h->pd, torque, h->bb, n, (double*)up, (double*)wp, h->side, &h->launches);
+  else
+    launch_pair_f32(h->gf, h->pf, h->ptab, torque, h->bb, n, (float*)up, (float*)wp, h->side, &h->launches);
+  if ((rc = stage_end(h, t_pair, h->side))) return rc;
+  FCM_CUDA(cudaGetLastError());
+  FCM_CUDA(cudaEventRecord(h->ev_join, h->side));
+  return FCM_OK;
+}
+
 template <typename R>
 int run(fcm_handle* h, int n, const R* pos, const R* F, const R* T, R* U, R* W, int stages, bool spread_only,
         cudaStream_t s) {
@@ -394,26 +416,12 @@ int run(fcm_handle* h, int n, const R* pos, const R* F, const R* T, R* U, R* W, 
   const bool grid_on = spread_only || (stages & FCM_STAGE_GRID);
   const bool pair_on = !spread_only && (stages & FCM_STAGE_PAIR) && h->pairs_on;
   const Geometry<R>& g = *reinterpret_cast<const Geometry<R>*>(h->fp64 ? (const void*)&h->gd : (const void*)&h->gf);
-  int rc, t_all, t_bin, t_pair, t_spread, t_fft, t_gather;
+  int rc, t_all, t_bin, t_spread, t_fft, t_gather;
   if ((rc = stage_begin(h, 5, s, &t_all))) return rc;
   if ((rc = stage_begin(h, 0, s, &t_bin))) return rc;
   launch_binning<R>(g, n, pos, F, T, h->bb, pair_on, s, &h->launches);
   if ((rc = stage_end(h, t_bin, s))) return rc;
   FCM_CUDA(cudaGetLastError());
-  if (pair_on) {
-    R* up = grid_on ? (R*)h->upair : U;
-    R* wp = grid_on ? (R*)h->wpair : Wout;
-    FCM_CUDA(cudaEventRecord(h->ev_fork, s));
-    FCM_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
-    if ((rc = stage_begin(h, 4, h->side, &t_pair))) return rc;
-    if (h->fp64)
-      launch_pair_f64(h->gd, h->pd, torque, h->bb, n, (double*)up, (double*)wp, h->side, &h->launches);
-    else
-      launch_pair_f32(h->gf, h->pf, h->ptab, torque, h->bb, n, (float*)up, (float*)wp, h->side, &h->launches);
-    if ((rc = stage_end(h, t_pair, h->side))) return rc;
-    FCM_CUDA(cudaGetLastError());
-    FCM_CUDA(cudaEventRecord(h->ev_join, h->side));
-  }
   if (grid_on) {
     launch_zero(h->grid, h->grid_bytes, s, &h->launches);
     if ((rc = stage_begin(h, 1, s, &t_spread))) return rc;
@@ -423,6 +431,9 @@ int run(fcm_handle* h, int n, const R* pos, const R* F, const R* T, R* U, R* W, 
       launch_spread_f32(h->gf, h->kf, torque, h->p.spread_kernel, h->bb, (float*)h->grid, s, &h->launches);
     if ((rc = stage_end(h, t_spread, s))) return rc;
     FCM_CUDA(cudaGetLastError());
+    if (pair_on && !spread_only) {
+      if ((rc = launch_pair_stage(h, n, U, Wout, torque, grid_on, s))) return rc;
+    }
     if (!spread_only) {
       if ((rc = stage_begin(h, 2, s, &t_fft))) return rc;
       FCM_CUFFT(cufftSetStream(h->r2c, s));
@@ -452,6 +463,7 @@ int run(fcm_handle* h, int n, const R* pos, const R* F, const R* T, R* U, R* W, 
       FCM_CUDA(cudaGetLastError());
     }
   } else if (pair_on) {
+    if ((rc = launch_pair_stage(h, n, U, Wout, torque, grid_on, s))) return rc;
     FCM_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
   } else if (!spread_only) {  // only the correction requested and it is identically zero
     launch_zero(U, sizeof(R) * 3 * (size_t)n, s, &h->launches);
