@@ -21,7 +21,7 @@ __global__ void __launch_bounds__(256) key_count_kernel(Geometry<R> g, int n, co
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     R y = wrap_coord(pos[3 * (size_t)i + d], g.L[d], &bad);
-    int i0 = pmod(window_start(y, g.h[d], g.MG), g.M[d]);
+    int i0 = pmod(window_start_d(g, d, y), g.M[d]);
     t[d] = i0 / g.tile[d];
     c[d] = cell_coord(y, g.cellw_inv[d], g.mcell[d]);
   }

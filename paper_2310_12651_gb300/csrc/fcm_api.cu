@@ -304,6 +304,7 @@ void fill_geometry(const fcm_params& p, const int tile[3], Geometry<R>* g) {
   for (int d = 0; d < 3; ++d) {
     g->L[d] = (R)p.L[d];
     g->h[d] = (R)(p.L[d] / p.M[d]);
+    g->inv_h[d] = (R)(p.M[d] / p.L[d]);
     g->M[d] = p.M[d];
     g->tile[d] = tile[d];
     g->ntile[d] = (p.M[d] + tile[d] - 1) / tile[d];

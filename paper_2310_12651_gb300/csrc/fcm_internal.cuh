@@ -49,6 +49,7 @@ template <typename R>
 struct Geometry {
   R L[3];        // box edges
   R h[3];        // grid spacing L_i / M_i
+  R inv_h[3];    // M_i / L_i
   R cellw_inv[3];// m_i / L_i (pair cells)
   int M[3];      // grid points
   int MG;        // grid support per dimension
@@ -68,13 +69,24 @@ __device__ inline R wrap_coord(R y, R L, int* bad) {
   return w;
 }
 
-// First grid index of the M_G-point window: floor(y/h - M_G/2) + 1 (unwrapped).
+// First grid index of the M_G-point window: floor(y/h - M_G/2) + 1 (unwrapped),
+// from s = y/h. The FP32 path forms s = y * (1/h) and the FP64 path s = y / h;
+// every site of one precision goes through window_start_d, so they all agree.
 template <typename R>
-__device__ inline int window_start(R y, R h, int MG) {
-  R v = x_floor(y / h - R(0.5) * R(MG));
-  v = fmax(fmin(v, R(1 << 29)), R(-(1 << 29)));
+__device__ inline int window_start_scaled(R s, int MG) {
+  R v = x_floor(s - R(0.5) * R(MG));
+  v = v < R(-(1 << 29)) ? R(-(1 << 29)) : (v > R(1 << 29) ? R(1 << 29) : v);
   return (int)v + 1;
 }
+__device__ inline int window_start_d(const Geometry<float>& g, int d, float y) {
+  return window_start_scaled(y * g.inv_h[d], g.MG);
+}
+__device__ inline int window_start_d(const Geometry<double>& g, int d, double y) {
+  return window_start_scaled(y / g.h[d], g.MG);
+}
+
+// i mod M for i in (-M, 2M): one correction instead of an integer division.
+__host__ __device__ inline int wrap_once(int i, int M) { return i < 0 ? i + M : (i >= M ? i - M : i); }
 
 __host__ __device__ inline int pmod(int i, int m) { int r = i % m; return r < 0 ? r + m : r; }
 

@@ -15,11 +15,6 @@
 
 namespace fcm {
 
-__device__ inline void cp_async4(float* smem_dst, const float* gmem_src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gmem_src) : "memory");
-}
-
 template <int MGT, bool GUARD, bool TORQUE, bool SAMEW>
 __global__ void __launch_bounds__(256) gather_tile_kernel(Geometry<float> g, KernelConsts<float> kc,
                                                           const float4* __restrict__ pos,
@@ -36,26 +31,17 @@ __global__ void __launch_bounds__(256) gather_tile_kernel(Geometry<float> g, Ker
   const TileOrigin o = tile_origin(g, t);
   const int MG = GUARD ? g.MG : MGT;
   const ExtLayout l = ext_layout(g.tile, MG);
-  const size_t Mtot = (size_t)g.M[0] * g.M[1] * g.M[2];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  {
-    const bool has_x = lane < l.EX;
-    const int gx = wrap_index(o.ox0 + lane, g.M[0]);
-    for (RowWalk rw = row_walk_begin(g, o, l); rw.r < rw.r1; row_walk_next(g, o, l, rw)) {
-      if (has_x)
-        cp_async4(acc + rw.c * l.C + rw.ez * l.Q + rw.ey * l.P + lane,
-                  grid + rw.c * Mtot + ((size_t)rw.gz * g.M[1] + rw.gy) * g.M[0] + gx);
-    }
-    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-  }
+  stage_region_async(g, o, l, grid, acc);
   __syncthreads();
 
   for (int p = p0 + warp; p < p1; p += nwarp) {
     const float4 y = pos[p];
-    const int4 off = window_offset(g, o, y);
-    const float dxl = (float)(window_start(y.x, g.h[0], MG) + lane) * g.h[0] - y.x;
-    const float dyl = (float)(window_start(y.y, g.h[1], MG) + lane) * g.h[1] - y.y;
-    const float dzl = (float)(window_start(y.z, g.h[2], MG) + lane) * g.h[2] - y.z;
+    const int3 i0 = window_starts(g, y);
+    const int4 off = window_offset(g, o, i0);
+    const float dxl = (float)(i0.x + lane) * g.h[0] - y.x;
+    const float dyl = (float)(i0.y + lane) * g.h[1] - y.y;
+    const float dzl = (float)(i0.z + lane) * g.h[2] - y.z;
     const float gxl = expf(-dxl * dxl * kc.inv2S2);
     const float gyl = expf(-dyl * dyl * kc.inv2S2);
     const float gzl = expf(-dzl * dzl * kc.inv2S2);
@@ -75,8 +61,14 @@ __global__ void __launch_bounds__(256) gather_tile_kernel(Geometry<float> g, Ker
     }
     float u0 = 0.f, u1 = 0.f, u2 = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f;
     int jy = lane, jz = 0;
-    while (jy >= MG) { jy -= MG; ++jz; }
+    if (GUARD) {
+      while (jy >= MG) { jy -= MG; ++jz; }
+    }
     for (int r0 = 0; r0 < MG * MG; r0 += 32) {
+      if (!GUARD) {  // window row r = jy + M_G jz, division by a compile-time constant
+        jz = (r0 + lane) / MGT;
+        jy = r0 + lane - jz * MGT;
+      }
       const bool active = r0 + lane < MG * MG;
       const int sy = active ? jy : 0, sz = active ? jz : 0;
       const float dy = __shfl_sync(kFullMask32, dyl, sy);
@@ -116,8 +108,10 @@ __global__ void __launch_bounds__(256) gather_tile_kernel(Geometry<float> g, Ker
           w2 = fmaf(H, dy1 - dy * dx0, w2);
         }
       }
-      jy += 32;
-      while (jy >= MG) { jy -= MG; ++jz; }
+      if (GUARD) {
+        jy += 32;
+        while (jy >= MG) { jy -= MG; ++jz; }
+      }
     }
 #pragma unroll
     for (int s = 16; s > 0; s >>= 1) {

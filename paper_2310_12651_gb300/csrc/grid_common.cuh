@@ -58,53 +58,71 @@ __device__ inline int wrap_index(int i, int M) {
   return i;
 }
 
-// Window start of a particle inside the extended region (clamped into the tile).
-__device__ inline int4 window_offset(const Geometry<float>& g, const TileOrigin& o, float4 y) {
+// Window start (unwrapped grid index) of a particle along each axis.
+__device__ inline int3 window_starts(const Geometry<float>& g, float4 y) {
+  return make_int3(window_start_d(g, 0, y.x), window_start_d(g, 1, y.y), window_start_d(g, 2, y.z));
+}
+
+// Window start inside the extended region (clamped into the tile). Positions are
+// wrapped into [0, L), so the window start lies in (-M, M) and one correction wraps it.
+__device__ inline int4 window_offset(const Geometry<float>& g, const TileOrigin& o, int3 i0) {
   int4 off;
-  off.x = min(max(pmod(window_start(y.x, g.h[0], g.MG), g.M[0]) - o.ox0, 0), g.tile[0] - 1);
-  off.y = min(max(pmod(window_start(y.y, g.h[1], g.MG), g.M[1]) - o.oy0, 0), g.tile[1] - 1);
-  off.z = min(max(pmod(window_start(y.z, g.h[2], g.MG), g.M[2]) - o.oz0, 0), g.tile[2] - 1);
+  off.x = min(max(wrap_once(i0.x, g.M[0]) - o.ox0, 0), g.tile[0] - 1);
+  off.y = min(max(wrap_once(i0.y, g.M[1]) - o.oy0, 0), g.tile[1] - 1);
+  off.z = min(max(wrap_once(i0.z, g.M[2]) - o.oz0, 0), g.tile[2] - 1);
   off.w = 0;
   return off;
 }
 
-// Rows (c, z, y) of the extended region visited by one warp as a contiguous
-// block: one division at the start, then carries. gy, gz are the wrapped grid
-// coordinates of the row. Lane l owns x offset l (EX <= 31).
-struct RowWalk {
-  int c, ez, ey, gy, gz, r, r1;
-};
-
-__device__ inline RowWalk row_walk_begin(const Geometry<float>& g, const TileOrigin& o, const ExtLayout& l) {
-  const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  const int rows = 3 * l.EY * l.EZ;
-  const int per = (rows + nwarp - 1) / nwarp;
-  RowWalk w;
-  w.r = min(warp * per, rows);
-  w.r1 = min(w.r + per, rows);
-  w.c = w.r / (l.EY * l.EZ);
-  const int rem = w.r - w.c * l.EY * l.EZ;
-  w.ez = rem / l.EY;
-  w.ey = rem - w.ez * l.EY;
-  w.gy = wrap_index(o.oy0 + w.ey, g.M[1]);
-  w.gz = wrap_index(o.oz0 + w.ez, g.M[2]);
-  return w;
+// Copies the extended region of the grid (3 components) into shared memory with
+// asynchronous 4-byte copies: warps take (component, z) planes, lanes take x,
+// rows advance with incremental offsets.
+__device__ inline void stage_region_async(const Geometry<float>& g, const TileOrigin& o, const ExtLayout& l,
+                                          const float* __restrict__ grid, float* ext) {
+  const size_t Mtot = (size_t)g.M[0] * g.M[1] * g.M[2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  if (lane < l.EX) {
+    const int gx = wrap_index(o.ox0 + lane, g.M[0]);
+    const int gy0 = wrap_index(o.oy0, g.M[1]);
+    for (int pl = warp; pl < 3 * l.EZ; pl += nwarp) {
+      const int c = pl / l.EZ;
+      const int ez = pl - c * l.EZ;
+      const int gz = wrap_index(o.oz0 + ez, g.M[2]);
+      const float* gplane = grid + c * Mtot + (size_t)gz * g.M[1] * g.M[0] + gx;
+      const unsigned sbase = (unsigned)__cvta_generic_to_shared(ext + c * l.C + ez * l.Q + lane);
+      int gy = gy0;
+      for (int ey = 0; ey < l.EY; ++ey) {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sbase + 4u * (unsigned)(ey * l.P)),
+                     "l"(gplane + (size_t)gy * g.M[0])
+                     : "memory");
+        gy = (gy + 1 == g.M[1]) ? 0 : gy + 1;
+      }
+    }
+  }
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
-__device__ inline void row_walk_next(const Geometry<float>& g, const TileOrigin& o, const ExtLayout& l, RowWalk& w) {
-  ++w.r;
-  if (++w.ey == l.EY) {
-    w.ey = 0;
-    w.gy = wrap_index(o.oy0, g.M[1]);
-    if (++w.ez == l.EZ) {
-      w.ez = 0;
-      ++w.c;
-      w.gz = wrap_index(o.oz0, g.M[2]);
-    } else {
-      w.gz = (w.gz + 1 == g.M[2]) ? 0 : w.gz + 1;
+// Adds the extended region held in shared memory to the grid: warps take
+// (component, z) planes, lanes take x, coalesced global reductions, zeros skipped.
+__device__ inline void flush_region(const Geometry<float>& g, const TileOrigin& o, const ExtLayout& l,
+                                    const float* ext, float* __restrict__ grid) {
+  const size_t Mtot = (size_t)g.M[0] * g.M[1] * g.M[2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  if (lane >= l.EX) return;
+  const int gx = wrap_index(o.ox0 + lane, g.M[0]);
+  const int gy0 = wrap_index(o.oy0, g.M[1]);
+  for (int pl = warp; pl < 3 * l.EZ; pl += nwarp) {
+    const int c = pl / l.EZ;
+    const int ez = pl - c * l.EZ;
+    const int gz = wrap_index(o.oz0 + ez, g.M[2]);
+    float* gplane = grid + c * Mtot + (size_t)gz * g.M[1] * g.M[0] + gx;
+    const float* splane = ext + c * l.C + ez * l.Q + lane;
+    int gy = gy0;
+    for (int ey = 0; ey < l.EY; ++ey) {
+      const float v = splane[ey * l.P];
+      if (v != 0.f) atomicAdd(gplane + (size_t)gy * g.M[0], v);
+      gy = (gy + 1 == g.M[1]) ? 0 : gy + 1;
     }
-  } else {
-    w.gy = (w.gy + 1 == g.M[1]) ? 0 : w.gy + 1;
   }
 }
 

@@ -121,6 +121,7 @@ extern "C" int fcm_pair_correction_noalloc(const fcm_params* p, int n, const voi
     g.L[d] = (float)p->L[d];
     g.M[d] = 1;  // one spread tile covering everything: only the pair cells are used here
     g.h[d] = (float)p->L[d];
+    g.inv_h[d] = (float)(1.0 / p->L[d]);
     g.tile[d] = 1;
     g.ntile[d] = 1;
     g.mcell[d] = std::max((int)(p->L[d] / p->r_c), 3);

@@ -25,7 +25,7 @@ __device__ inline void fill_tables(const Geometry<double>& g, const KernelConsts
   if (threadIdx.x < 3) {
     const int d = threadIdx.x;
     const double yd = d == 0 ? y.x : (d == 1 ? y.y : y.z);
-    t.i0[d] = window_start(yd, g.h[d], g.MG);
+    t.i0[d] = window_start_d(g, d, yd);
   }
   __syncthreads();
   for (int k = threadIdx.x; k < 3 * g.MG; k += blockDim.x) {

@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(rows_threads(MGT), 1) spread_rows_kernel(Geome
       const float h = g.h[d];
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
       if (j < MG) {
-        const float dd = (float)(window_start(yd, h, MG) + j) * h - yd;
+        const float dd = (float)(window_start_d(g, d, yd) + j) * h - yd;
         const float gs = expf(-dd * dd * kc.inv2S2);
         const float gd = SAMEW ? gs : expf(-dd * dd * kc.inv2SD2);
         v = (d == 0) ? make_float4(gs, dd * dd * gs, dd * gd, gd) : make_float4(gs, dd, gd, 0.f);
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(rows_threads(MGT), 1) spread_rows_kernel(Geome
       (d == 0 ? tb.xt : (d == 1 ? tb.yt : tb.zt))[q * MGT + j] = v;
     }
     for (int q = threadIdx.x; q < np; q += blockDim.x) {
-      tb.po[q] = window_offset(g, o, pos[base + q]);
+      tb.po[q] = window_offset(g, o, window_starts(g, pos[base + q]));
       tb.pf[q] = Fv[base + q];
       tb.pt[q] = TORQUE ? Tv[base + q] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
@@ -206,11 +206,12 @@ __global__ void __launch_bounds__(256) spread_tile_kernel(Geometry<float> g, Ker
     const float4 f = Fv[p];
     float4 tq = make_float4(0.f, 0.f, 0.f, 0.f);
     if (TORQUE) tq = Tv[p];
-    const int4 off = window_offset(g, o, y);
+    const int3 i0 = window_starts(g, y);
+    const int4 off = window_offset(g, o, i0);
     // lane l < MG holds the l-th point of each axis
-    const float dxl = (float)(window_start(y.x, g.h[0], MG) + lane) * g.h[0] - y.x;
-    const float dyl = (float)(window_start(y.y, g.h[1], MG) + lane) * g.h[1] - y.y;
-    const float dzl = (float)(window_start(y.z, g.h[2], MG) + lane) * g.h[2] - y.z;
+    const float dxl = (float)(i0.x + lane) * g.h[0] - y.x;
+    const float dyl = (float)(i0.y + lane) * g.h[1] - y.y;
+    const float dzl = (float)(i0.z + lane) * g.h[2] - y.z;
     const float gxl = expf(-dxl * dxl * kc.inv2S2);
     const float gyl = expf(-dyl * dyl * kc.inv2S2);
     const float gzl = expf(-dzl * dzl * kc.inv2S2);
@@ -278,14 +279,7 @@ __global__ void __launch_bounds__(256) spread_tile_kernel(Geometry<float> g, Ker
     }
   }
   __syncthreads();
-  const size_t Mtot = (size_t)g.M[0] * g.M[1] * g.M[2];
-  const bool has_x = lane < l.EX;
-  const int gxw = wrap_index(o.ox0 + lane, g.M[0]);
-  for (RowWalk w = row_walk_begin(g, o, l); w.r < w.r1; row_walk_next(g, o, l, w)) {
-    if (!has_x) continue;
-    const float v = acc[w.c * l.C + w.ez * l.Q + w.ey * l.P + lane];
-    if (v != 0.f) atomicAdd(grid + w.c * Mtot + ((size_t)w.gz * g.M[1] + w.gy) * g.M[0] + gxw, v);
-  }
+  flush_region(g, o, l, acc, grid);
 }
 
 // ---------------------------------------------------------------- sizing and launch
