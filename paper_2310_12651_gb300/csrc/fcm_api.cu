@@ -313,6 +313,7 @@ void fill_geometry(const fcm_params& p, const int tile[3], Geometry<R>* g) {
     g->mcell[d] = (int)std::min(std::max(m, 3.0), 1048576.0);
     g->cellw_inv[d] = (R)(g->mcell[d] / p.L[d]);
   }
+  g->shift = (g->mcell[0] >= 4 && g->mcell[1] >= 4 && g->mcell[2] >= 4) ? 1 : 0;
   g->MG = p.M_G;
 }
 

@@ -56,6 +56,8 @@ struct Geometry {
   int tile[3];   // spread/gather tile in grid points
   int ntile[3];  // ceil(M_i / tile_i)
   int mcell[3];  // pair cells per dimension, max(int(L_i / r_c), 3)
+  int shift;     // 1 if every mcell >= 4: the 27-cell neighbourhood never meets itself, so a
+                 // neighbour cell's periodic image relative to the centre cell is unique
 };
 
 // Position wrapped into [0, L): y - L floor(y / L), with the product rounded on

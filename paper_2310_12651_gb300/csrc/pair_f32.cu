@@ -10,27 +10,31 @@
 // contiguous in the cell-sorted arrays, so a warp walks at most 9 ranges (more
 // only where x wraps).
 //
-// GB300 decomposition: one warp per particle n. Lanes test 32 candidates at a
-// time; hits are compacted with a ballot into a per-warp shared-memory queue,
-// and the correction is evaluated when 32 hits are queued, so that work runs
-// with every lane busy although only ~15% of candidates are within r_c.
-// Per-lane sums are compensated (Neumaier); the warp reduction is a tree.
+// GB300 decomposition: one CTA per pair cell stages the candidates of the 27
+// neighbour cells in shared memory; a warp takes one particle n at a time.
+// Lanes test 32 candidates at a time; hits are compacted with a ballot into a
+// per-warp shared-memory queue, and the correction is evaluated when 32 hits
+// are queued, so that work runs with every lane busy although only ~15% of
+// candidates are within r_c. Per-lane sums are compensated (Neumaier), the
+// warp reduction is a tree, and the per-particle totals over candidate chunks
+// are compensated again.
 #include "fcm_internal.cuh"
 
 namespace fcm {
 
 constexpr unsigned kFullMask = 0xffffffffu;
-constexpr int kPairWarps = 8;
 constexpr int kQueue = 64;
 
+// Compensated (Kahan) running sum: c carries the low-order part lost by s.
 struct Neu {
   float s, c;
   __device__ inline void add(float v) {
-    float t = s + v;
-    c += (fabsf(s) >= fabsf(v)) ? ((s - t) + v) : ((v - t) + s);
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
     s = t;
   }
-  __device__ inline float value() const { return s + c; }
+  __device__ inline float value() const { return s - c; }
 };
 
 __device__ inline float min_image(float d, float L) {
@@ -65,119 +69,207 @@ __device__ inline void eval_pair(const PairConsts<float>& pc, const PairTable& t
   u[2].add(u2);
 }
 
+// ---------------------------------------------------------------- cell-tiled kernel
+//
+// One CTA per pair cell. The candidates of its 27 neighbour cells are staged
+// once in shared memory (positions, forces, torques; chunks of kCandChunk),
+// then each warp takes particles of the cell and runs the same ballot
+// compaction over the staged candidates: candidate reads are shared-memory
+// loads instead of L2 traffic repeated for every particle of the cell.
+
+constexpr int kCellWarps = 8;
+constexpr int kCandChunk = 1536;
+constexpr int kIBatch = 256;
+constexpr int kMaxPieces = 18;
+
 template <bool TORQUE>
-__global__ void __launch_bounds__(kPairWarps * 32) pair_warp_kernel(Geometry<float> g, PairConsts<float> pc, PairTable tab, int n,
-                                                                    const float4* __restrict__ cpos,
-                                                                    const float4* __restrict__ cF,
-                                                                    const float4* __restrict__ cT,
-                                                                    const int* __restrict__ cstart,
-                                                                    float* __restrict__ Uo,
-                                                                    float* __restrict__ Wo) {
-  __shared__ float4 qd[kPairWarps][kQueue];
-  __shared__ int qj[kPairWarps][kQueue];
+constexpr size_t cell_kernel_smem() {
+  return sizeof(float4) * (size_t)kCandChunk * (TORQUE ? 3 : 2) + sizeof(float) * 12 * kIBatch +
+         sizeof(float4) * kCellWarps * kQueue + sizeof(int) * kCellWarps * kQueue + sizeof(int) * 64 +
+         sizeof(float4) * kMaxPieces;
+}
+
+__device__ inline void neu_add(float* s, float* c, float v) {
+  const float t = *s + v;
+  *c += (fabsf(*s) >= fabsf(v)) ? ((*s - t) + v) : ((v - t) + *s);
+  *s = t;
+}
+
+template <bool TORQUE, bool SHIFT>
+__global__ void __launch_bounds__(kCellWarps * 32, 2) pair_cell_kernel(Geometry<float> g, PairConsts<float> pc,
+                                                                       PairTable tab,
+                                                                       const float4* __restrict__ cpos,
+                                                                       const float4* __restrict__ cF,
+                                                                       const float4* __restrict__ cT,
+                                                                       const int* __restrict__ cstart,
+                                                                       float* __restrict__ Uo,
+                                                                       float* __restrict__ Wo) {
+  extern __shared__ float4 sm4[];
+  float4* spos = sm4;
+  float4* sF = spos + kCandChunk;
+  float4* sT = sF + kCandChunk;
+  float* acc = reinterpret_cast<float*>(TORQUE ? sT + kCandChunk : sT);   // [kIBatch][12]
+  float4* qd = reinterpret_cast<float4*>(acc + 12 * kIBatch);               // [warps][kQueue]
+  int* qj = reinterpret_cast<int*>(qd + kCellWarps * kQueue);               // [warps][kQueue]
+  int* meta = qj + kCellWarps * kQueue;                                     // pieces: source start, prefix
+  float4* pshift = reinterpret_cast<float4*>(meta + 64);                    // periodic image shift per piece
+
+  const int cell = blockIdx.x;
+  const int i_begin = cstart[cell], i_end = cstart[cell + 1];
+  if (i_begin >= i_end) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int i = blockIdx.x * kPairWarps + warp;
-  if (i >= n) return;
-  const float4 yi = cpos[i];
-  const int cx = cell_coord(yi.x, g.cellw_inv[0], g.mcell[0]);
-  const int cy = cell_coord(yi.y, g.cellw_inv[1], g.mcell[1]);
-  const int cz = cell_coord(yi.z, g.cellw_inv[2], g.mcell[2]);
   const int mx = g.mcell[0], my = g.mcell[1], mz = g.mcell[2];
+  if (threadIdx.x == 0) {
+    const int cx = cell % mx, cy = (cell / mx) % my, cz = cell / (mx * my);
+    int np = 0, total = 0;
+    for (int ddz = -1; ddz <= 1; ++ddz) {
+      const int zu = cz + ddz;
+      const int zc = pmod(zu, mz);
+      const float sz = zu < 0 ? -g.L[2] : (zu >= mz ? g.L[2] : 0.f);
+      for (int ddy = -1; ddy <= 1; ++ddy) {
+        const int yu = cy + ddy;
+        const float sy = yu < 0 ? -g.L[1] : (yu >= my ? g.L[1] : 0.f);
+        const int rowbase = mx * (pmod(yu, my) + my * zc);
+        int ra[2], rb[2], k = 0;
+        float sx[2] = {0.f, 0.f};
+        if (cx - 1 >= 0 && cx + 1 < mx) { ra[0] = cx - 1; rb[0] = cx + 1; k = 1; }
+        else if (cx - 1 < 0) { ra[0] = mx - 1; rb[0] = mx - 1; sx[0] = -g.L[0]; ra[1] = 0; rb[1] = 1; k = 2; }
+        else { ra[0] = mx - 2; rb[0] = mx - 1; ra[1] = 0; rb[1] = 0; sx[1] = g.L[0]; k = 2; }
+        for (int q = 0; q < k; ++q) {
+          const int a = cstart[rowbase + ra[q]], b = cstart[rowbase + rb[q] + 1];
+          meta[2 * np] = a;
+          meta[2 * np + 1] = total;
+          pshift[np] = make_float4(sx[q], sy, sz, 0.f);
+          total += b - a;
+          ++np;
+        }
+      }
+    }
+    meta[2 * np + 1] = total;   // prefix sentinel
+    meta[63] = np;
+  }
+  __syncthreads();
+  const int npieces = meta[63];
+  const int total = meta[2 * npieces + 1];
   const unsigned lt = (1u << lane) - 1u;
-  Neu u[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-  Neu w[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-  int qh = 0, qn = 0;
-  for (int ddz = -1; ddz <= 1; ++ddz) {
-    const int zc = pmod(cz + ddz, mz);
-    for (int ddy = -1; ddy <= 1; ++ddy) {
-      const int yc = pmod(cy + ddy, my);
-      const int rowbase = mx * (yc + my * zc);
-      // x neighbours cx-1, cx, cx+1 as at most two contiguous cell ranges
-      int ra[2], rb[2], np = 0;
-      if (cx - 1 >= 0 && cx + 1 < mx) { ra[0] = cx - 1; rb[0] = cx + 1; np = 1; }
-      else if (cx - 1 < 0) { ra[0] = mx - 1; rb[0] = mx - 1; ra[1] = 0; rb[1] = 1; np = 2; }
-      else { ra[0] = mx - 2; rb[0] = mx - 1; ra[1] = 0; rb[1] = 0; np = 2; }
-      for (int piece = 0; piece < np; ++piece) {
-        const int a = cstart[rowbase + ra[piece]];
-        const int b = cstart[rowbase + rb[piece] + 1];
-        for (int base = a; base < b; base += 32) {
+  float4* myqd = qd + warp * kQueue;
+  int* myqj = qj + warp * kQueue;
+
+  for (int ib = i_begin; ib < i_end; ib += kIBatch) {
+    const int ni = min(kIBatch, i_end - ib);
+    for (int k = threadIdx.x; k < 12 * ni; k += blockDim.x) acc[k] = 0.f;
+    for (int cb = 0; cb < total; cb += kCandChunk) {
+      const int nc = min(kCandChunk, total - cb);
+      __syncthreads();
+      for (int q = 0; q < npieces; ++q) {
+        const int lo = max(meta[2 * q + 1], cb), hi = min(meta[2 * q + 3], cb + nc);
+        const int src = meta[2 * q] + (lo - meta[2 * q + 1]);
+        const float4 sh = pshift[q];
+        for (int k = threadIdx.x; k < hi - lo; k += blockDim.x) {
+          float4 y = cpos[src + k];
+          if (SHIFT) { y.x += sh.x; y.y += sh.y; y.z += sh.z; }
+          spos[lo - cb + k] = y;
+          sF[lo - cb + k] = cF[src + k];
+          if (TORQUE) sT[lo - cb + k] = cT[src + k];
+        }
+      }
+      __syncthreads();
+      for (int il = warp; il < ni; il += kCellWarps) {
+        const float4 yi = cpos[ib + il];
+        const int self = __float_as_int(yi.w);
+        Neu u[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        Neu w[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        int qh = 0, qn = 0;
+        for (int base = 0; base < nc; base += 32) {
           const int j = base + lane;
           bool hit = false;
           float4 dq = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (j < b && j != i) {
-            const float4 yj = cpos[j];
-            dq.x = min_image(yi.x - yj.x, g.L[0]);
-            dq.y = min_image(yi.y - yj.y, g.L[1]);
-            dq.z = min_image(yi.z - yj.z, g.L[2]);
-            dq.w = dq.x * dq.x + dq.y * dq.y + dq.z * dq.z;
-            hit = dq.w < pc.rc2;
+          if (j < nc) {
+            const float4 yj = spos[j];
+            if (__float_as_int(yj.w) != self) {
+              dq.x = SHIFT ? yi.x - yj.x : min_image(yi.x - yj.x, g.L[0]);
+              dq.y = SHIFT ? yi.y - yj.y : min_image(yi.y - yj.y, g.L[1]);
+              dq.z = SHIFT ? yi.z - yj.z : min_image(yi.z - yj.z, g.L[2]);
+              dq.w = dq.x * dq.x + dq.y * dq.y + dq.z * dq.z;
+              hit = dq.w < pc.rc2;
+            }
           }
           const unsigned m = __ballot_sync(kFullMask, hit);
           if (hit) {
             const int slot = (qh + qn + __popc(m & lt)) & (kQueue - 1);
-            qd[warp][slot] = dq;
-            qj[warp][slot] = j;
+            myqd[slot] = dq;
+            myqj[slot] = j;
           }
           qn += __popc(m);
           __syncwarp();
           if (qn >= 32) {
             const int slot = (qh + lane) & (kQueue - 1);
-            const float4 e = qd[warp][slot];
-            const int jj = qj[warp][slot];
-            const float4 Fj = cF[jj];
-            float4 Tj = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (TORQUE) Tj = cT[jj];
-            eval_pair<TORQUE>(pc, tab, e, Fj, Tj, u, w);
+            const int jj = myqj[slot];
+            eval_pair<TORQUE>(pc, tab, myqd[slot], sF[jj], TORQUE ? sT[jj] : make_float4(0.f, 0.f, 0.f, 0.f), u, w);
             qh = (qh + 32) & (kQueue - 1);
             qn -= 32;
             __syncwarp();
           }
         }
+        if (lane < qn) {
+          const int slot = (qh + lane) & (kQueue - 1);
+          const int jj = myqj[slot];
+          eval_pair<TORQUE>(pc, tab, myqd[slot], sF[jj], TORQUE ? sT[jj] : make_float4(0.f, 0.f, 0.f, 0.f), u, w);
+        }
+        __syncwarp();
+        float r[6] = {u[0].value(), u[1].value(), u[2].value(), w[0].value(), w[1].value(), w[2].value()};
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+          for (int c = 0; c < 6; ++c) r[c] += __shfl_xor_sync(kFullMask, r[c], o);
+        }
+        if (lane == 0) {
+          float* a = acc + 12 * il;
+#pragma unroll
+          for (int c = 0; c < 6; ++c) neu_add(a + c, a + 6 + c, r[c]);
+        }
       }
     }
-  }
-  if (lane < qn) {
-    const int slot = (qh + lane) & (kQueue - 1);
-    const float4 e = qd[warp][slot];
-    const int jj = qj[warp][slot];
-    const float4 Fj = cF[jj];
-    float4 Tj = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (TORQUE) Tj = cT[jj];
-    eval_pair<TORQUE>(pc, tab, e, Fj, Tj, u, w);
-  }
-  float r[6] = {u[0].value(), u[1].value(), u[2].value(), w[0].value(), w[1].value(), w[2].value()};
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-    for (int c = 0; c < 6; ++c) r[c] += __shfl_xor_sync(kFullMask, r[c], o);
-  }
-  if (lane == 0) {
-    const float4 Fi = cF[i];
-    const size_t o = 3 * (size_t)index_from_w(yi.w);
-    Uo[o + 0] = r[0] + pc.selfVF * Fi.x;
-    Uo[o + 1] = r[1] + pc.selfVF * Fi.y;
-    Uo[o + 2] = r[2] + pc.selfVF * Fi.z;
-    if (TORQUE && Wo) {
-      const float4 Ti = cT[i];
-      Wo[o + 0] = r[3] + pc.selfWT * Ti.x;
-      Wo[o + 1] = r[4] + pc.selfWT * Ti.y;
-      Wo[o + 2] = r[5] + pc.selfWT * Ti.z;
+    __syncthreads();
+    for (int il = threadIdx.x; il < ni; il += blockDim.x) {
+      const int i = ib + il;
+      const float* a = acc + 12 * il;
+      const float4 Fi = cF[i];
+      const size_t o = 3 * (size_t)index_from_w(cpos[i].w);
+      Uo[o + 0] = (a[0] + a[6]) + pc.selfVF * Fi.x;
+      Uo[o + 1] = (a[1] + a[7]) + pc.selfVF * Fi.y;
+      Uo[o + 2] = (a[2] + a[8]) + pc.selfVF * Fi.z;
+      if (TORQUE && Wo) {
+        const float4 Ti = cT[i];
+        Wo[o + 0] = (a[3] + a[9]) + pc.selfWT * Ti.x;
+        Wo[o + 1] = (a[4] + a[10]) + pc.selfWT * Ti.y;
+        Wo[o + 2] = (a[5] + a[11]) + pc.selfWT * Ti.z;
+      }
     }
+    __syncthreads();
   }
+}
+
+template <bool TORQUE, bool SHIFT>
+static void cell_variant(const Geometry<float>& g, const PairConsts<float>& pc, const PairTable& tab,
+                         const BinBuffers& b, float* upair, float* wpair, cudaStream_t s) {
+  const size_t smem = cell_kernel_smem<TORQUE>();
+  auto k = pair_cell_kernel<TORQUE, SHIFT>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k<<<b.ncells, kCellWarps * 32, smem, s>>>(g, pc, tab, (const float4*)b.c_pos, (const float4*)b.c_F,
+                                            (const float4*)b.c_T, b.cell_start, upair, wpair);
 }
 
 void launch_pair_f32(const Geometry<float>& g, const PairConsts<float>& pc, const PairTable& tab, bool torque,
                      const BinBuffers& b, int n, float* upair, float* wpair, cudaStream_t s, long long* launches) {
   if (n <= 0) return;
-  const int blocks = (n + kPairWarps - 1) / kPairWarps;
-  if (torque)
-    pair_warp_kernel<true><<<blocks, kPairWarps * 32, 0, s>>>(g, pc, tab, n, (const float4*)b.c_pos,
-                                                              (const float4*)b.c_F, (const float4*)b.c_T,
-                                                              b.cell_start, upair, wpair);
-  else
-    pair_warp_kernel<false><<<blocks, kPairWarps * 32, 0, s>>>(g, pc, tab, n, (const float4*)b.c_pos,
-                                                               (const float4*)b.c_F, (const float4*)b.c_T,
-                                                               b.cell_start, upair, wpair);
+  if (torque) {
+    if (g.shift) cell_variant<true, true>(g, pc, tab, b, upair, wpair, s);
+    else cell_variant<true, false>(g, pc, tab, b, upair, wpair, s);
+  } else {
+    if (g.shift) cell_variant<false, true>(g, pc, tab, b, upair, wpair, s);
+    else cell_variant<false, false>(g, pc, tab, b, upair, wpair, s);
+  }
   *launches += 1;
 }
 

@@ -129,6 +129,7 @@ extern "C" int fcm_pair_correction_noalloc(const fcm_params* p, int n, const voi
     cells *= g.mcell[d];
   }
   g.MG = 1;
+  g.shift = (g.mcell[0] >= 4 && g.mcell[1] >= 4 && g.mcell[2] >= 4) ? 1 : 0;
   if (cells > (long long)FCM_NOALLOC_MAX_CELLS)
     return fail(FCM_ERR_ARG, std::to_string(cells) + " pair cells exceed " + std::to_string(FCM_NOALLOC_MAX_CELLS) +
                                  " (the fixed scratch of the no-alloc path); r_c is too small for this box");
