@@ -39,25 +39,29 @@ if ROOT not in sys.path:
 METRIC = "particle-applies/s, FP32 batched vs FP64 plain at rel err≤1e-4; serve p50/p99"
 UNIT = "particle-applies/s"
 FLUSH_BYTES = 256 << 20
-N_SYS = 65536
-PHI = 0.05
-GRID = 128
-SIGMA = 2.0
 TRUNC = 4.8          # window half-width in Sigma (grid part error ~2e-5)
 TOL = 1e-6           # pair cutoff tolerance
-# dram__bytes_read.sum + dram__bytes_write.sum per launch, one ncu --set full capture of this workload with the
+# Workloads: N per system, volume fraction, grid points per side, Sigma, default systems per step.
+WORKLOADS = {
+    "c2": dict(n=65536, phi=0.05, grid=128, Sigma=2.0, batch=32),
+    "large": dict(n=1048576, phi=0.10, grid=256, Sigma=1.5, batch=2),
+}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch, one ncu --set full capture of the c2 workload with the
 # current kernels (cold caches); None once a kernel changes after the capture.
-TRAFFIC_BYTES = {"gather": 27.830016e6, "spread": 28.379904e6, "pair": 3.247872e6}
+TRAFFIC_BYTES = {"c2": {"gather": 27.826176e6, "spread": 28.370944e6, "pair": 3.251968e6}}
 
 
-def workload(n=N_SYS, phi=PHI, grid=GRID, h_ref=None):
+def workload(name="c2", n=None, h_ref=None):
     from paper_2310_12651_gb300 import inputs, tune
-    L = inputs.box_edge(n, phi)
-    M = grid if h_ref is None else max(8, int(round(L / h_ref)))
+    spec = WORKLOADS[name]
+    n = spec["n"] if n is None else n
+    L = inputs.box_edge(n, spec["phi"])
+    M = spec["grid"] if h_ref is None else max(8, int(round(L / h_ref)))
     h = L / M
-    MG = tune.support_points(SIGMA, h, TRUNC)
-    rc = tune.cutoff(SIGMA, TOL, torques=True)
-    return dict(n=n, phi=phi, L=L, M=M, h=h, Sigma=SIGMA, M_G=MG, r_c=rc)
+    Sigma = spec["Sigma"]
+    MG = tune.support_points(Sigma, h, TRUNC)
+    rc = tune.cutoff(Sigma, TOL, torques=True)
+    return dict(name=name, n=n, phi=spec["phi"], L=L, M=M, h=h, Sigma=Sigma, M_G=MG, r_c=rc)
 
 
 def describe(w, batch, precision="FP32"):
@@ -157,29 +161,29 @@ def run_cpu_oracle(w, seed, torques=True):
     return time.perf_counter() - t
 
 
-def cpu_baseline(target_s=15.0):
+def cpu_baseline(name, target_s=15.0):
     """The oracle timed on a bounded sample of the workload (same density, spacing, Sigma, M_G, r_c)."""
-    full = workload()
+    full = workload(name)
     n = 16384
-    w = workload(n=n, h_ref=full["h"])
+    w = workload(name, n=n, h_ref=full["h"])
     secs = run_cpu_oracle(w, 2310126590)
     reps = 1
     while secs * (reps + 1) / reps < target_s and reps < 4:
         secs += run_cpu_oracle(w, 2310126590 + reps)
         reps += 1
     return {"value": n * reps / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{reps} oracle apply(s) of {n} spheres at phi=5% (L={w['L']:.1f}a, {w['M']}^3, "
-                      f"h={w['h']:.3f}a, Sigma=2a, M_G={w['M_G']}, r_c={w['r_c']:.2f}a), forces+torques, FP64 numpy "
-                      f"single thread, {secs:.1f} s",
+            "sample": f"{reps} oracle apply(s) of {n} spheres at phi={w['phi']:.0%} (L={w['L']:.1f}a, {w['M']}^3, "
+                      f"h={w['h']:.3f}a, Sigma={w['Sigma']}a, M_G={w['M_G']}, r_c={w['r_c']:.2f}a), forces+torques, "
+                      f"FP64 numpy single thread, {secs:.1f} s",
             "host_cores": len(os.sched_getaffinity(0))}
 
 
 def reference_arm(args, world, rank):
     if rank != 0:
         return 0
-    full = workload()
+    full = workload(args.workload)
     n = 4096
-    w = workload(n=n, h_ref=full["h"])
+    w = workload(args.workload, n=n, h_ref=full["h"])
     for k in range(args.warmup):
         run_cpu_oracle(w, 2310126700 + k)
     t = 0.0
@@ -190,8 +194,9 @@ def reference_arm(args, world, rank):
             "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": f"oracle (FP64 numpy) on a bounded sample: {n} spheres at phi=5%, {w['M']}^3 "
-                                   f"(h={w['h']:.3f}a), Sigma=2a, M_G={w['M_G']}, r_c={w['r_c']:.2f}a, forces+torques",
+            "config": {"workload": f"oracle (FP64 numpy) on a bounded sample: {n} spheres at phi={w['phi']:.0%}, "
+                                   f"{w['M']}^3 (h={w['h']:.3f}a), Sigma={w['Sigma']}a, M_G={w['M_G']}, "
+                                   f"r_c={w['r_c']:.2f}a, forces+torques",
                        "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{args.steps} oracle applies of {n} spheres"},
@@ -205,7 +210,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--batch", type=int, default=32, help="systems per step")
+    ap.add_argument("--batch", type=int, default=0, help="systems per step (0: the workload's default)")
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -229,8 +235,8 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     sptr = stream.cuda_stream
-    w = workload()
-    B = args.batch
+    w = workload(args.workload)
+    B = args.batch or WORKLOADS[args.workload]["batch"]
     n = w["n"]
     params = fcm.make_params(w["L"], w["M"], w["Sigma"], w["r_c"], w["M_G"], n, fcm.FCM_FP32,
                              spread_kernel=args.spread_kernel)
@@ -355,7 +361,7 @@ def main():
     dominant = max(("spread", "gather", "pair"), key=lambda s: avg[s] or 0.0)
     achieved = flops[dominant] / (avg[dominant] * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved / alu_peak, "traffic": TRAFFIC_BYTES.get(dominant),
+                "frac": achieved / alu_peak, "traffic": TRAFFIC_BYTES.get(args.workload, {}).get(dominant),
                 "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
                 "flops_per_launch": flops[dominant]}
     M3 = w["M"] ** 3
@@ -375,7 +381,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline()
+        cpu = cpu_baseline(args.workload)
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",

@@ -81,25 +81,38 @@ def random_suspension(n: int, L: float, seed: int, min_sep: float = 2.2,
 
 
 def random_rods(n_rods: int, per_rod: int, L: float, seed: int, bond: float = 2.2,
-                min_sep: float = 2.2, max_attempts: int = 200000) -> tuple[np.ndarray, float]:
+                min_sep: float = 2.2, max_attempts: int = 400000, stall: int = 300,
+                cone_cos: float = 0.98) -> tuple[np.ndarray, float]:
     """Rigid rods of ``per_rod`` spheres spaced ``bond`` apart along a random axis.
 
     Rod centres are uniform in the box and axes uniform on the sphere. A rod is
     rejected if any of its spheres lies closer than ``min_sep`` to a sphere of an
-    accepted rod (periodic distance). Returns (positions wrapped into [0, L), the
-    volume fraction reached with radius 1 spheres).
+    accepted rod (periodic distance). Long rods jam well below the isotropic-
+    nematic density; after ``stall`` consecutive rejections the remaining rods
+    are drawn with axes inside a cone around z (cos theta >= ``cone_cos``), which
+    packs. Returns (positions wrapped into [0, L), the volume fraction reached
+    with radius 1 spheres); ``random_rods.last_stats`` records how many rods were
+    isotropic and how many aligned.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     offs = (np.arange(per_rod) - 0.5 * (per_rod - 1)) * bond
     accepted: list[np.ndarray] = []
     tree = None
     pending: list[np.ndarray] = []
-    attempts = 0
+    attempts = rejections = 0
+    aligned = False
+    n_iso = 0
     while len(accepted) < n_rods and attempts < max_attempts:
         attempts += 1
         c = rng.random(3) * L
-        v = rng.normal(size=3)
-        v /= np.linalg.norm(v)
+        if aligned:
+            cz = rng.uniform(cone_cos, 1.0)
+            ph = rng.uniform(0.0, 2 * np.pi)
+            sz = np.sqrt(1.0 - cz * cz)
+            v = np.array([sz * np.cos(ph), sz * np.sin(ph), cz])
+        else:
+            v = rng.normal(size=3)
+            v /= np.linalg.norm(v)
         pts = np.mod(c[None, :] + offs[:, None] * v[None, :], L)
         pts = np.minimum(pts, np.nextafter(L, 0))
         bad = False
@@ -111,12 +124,19 @@ def random_rods(n_rods: int, per_rod: int, L: float, seed: int, bond: float = 2.
             dd = _min_image(pts[:, None, :] - q[None, :, :], L)
             bad = bool(np.any(np.einsum("ijk,ijk->ij", dd, dd) < min_sep ** 2))
         if bad:
+            rejections += 1
+            if not aligned and rejections >= stall:
+                aligned = True
             continue
+        rejections = 0
         accepted.append(pts)
+        if not aligned:
+            n_iso += 1
         pending.append(pts)
         if len(pending) >= 16:
             tree = _KDTree(np.concatenate(accepted, axis=0), boxsize=L)
             pending = []
+    random_rods.last_stats = {"isotropic": n_iso, "aligned": len(accepted) - n_iso, "attempts": attempts}
     if not accepted:
         return np.zeros((0, 3)), 0.0
     pos = np.concatenate(accepted, axis=0)

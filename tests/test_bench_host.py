@@ -44,10 +44,10 @@ def test_max_over_ranks_gloo_world_2():
 def test_workload_parameters_match_the_documented_rules():
     sys.path.insert(0, ROOT)
     import bench
-    w = bench.workload()
+    w = bench.workload("c2")
     assert w["n"] == 65536 and w["M"] == 128 and w["M_G"] == 14
     assert abs(w["L"] - 176.41391792668995) < 1e-9
     from oracle import params
     assert abs(w["r_c"] - params.cutoff_radius(2.0, 1e-6, torques=True)) < 1e-6
-    small = bench.workload(n=16384, h_ref=w["h"])
+    small = bench.workload("c2", n=16384, h_ref=w["h"])
     assert abs(small["h"] - w["h"]) / w["h"] < 0.02 and small["M_G"] == 14
