@@ -5,13 +5,16 @@ One step = one pass of the whole hot path (binning, spread, FFT Stokes solve,
 gather, pair correction) over one batch of ``--batch`` independent periodic
 systems, each a seeded uniform suspension of N = 65,536 spheres at 5% volume
 fraction (L = 176.41a) on a 128^3 grid with Sigma = 2a, forces and torques,
-FP32. Every system's inputs stay resident in HBM; L2 is flushed (256 MB
-write) before every apply and each apply is timed with CUDA events on the
-stream it runs on. ``value`` = particles processed / summed apply time.
+FP32. The systems are stacked along the particle axis and the step is one
+fcm_batch_apply call (every stage one launch over all systems; ``--mode
+single`` runs one fcm_apply per system instead). Every system's inputs stay
+resident in HBM; L2 is flushed (256 MB write) before every step and each step
+is timed with CUDA events on the stream it runs on. ``value`` = particles
+processed / summed step time.
 
 ``e2e`` repeats the measurement through the same C-ABI call with host
 buffers: pinned host -> device copies of pos, F, T and device -> host copies of
-U, W inside each timed apply.
+U, W inside each timed step.
 
 ``--impl reference`` times the FP64 CPU oracle on the host cores instead, on a
 bounded sample of the same workload (same density, Sigma, M_G, r_c; fewer
@@ -46,9 +49,9 @@ WORKLOADS = {
     "c2": dict(n=65536, phi=0.05, grid=128, Sigma=2.0, batch=32),
     "large": dict(n=1048576, phi=0.10, grid=256, Sigma=1.5, batch=2),
 }
-# dram__bytes_read.sum + dram__bytes_write.sum per launch, one ncu --set full capture of the c2 workload with the
-# current kernels (cold caches); None once a kernel changes after the capture.
-TRAFFIC_BYTES = {"c2": {"gather": 27.826176e6, "spread": 28.370944e6, "pair": 3.251968e6}}
+# dram__bytes_read.sum + dram__bytes_write.sum per system of a launch (cold caches), from one ncu capture of
+# the current kernels; a launch over B systems moves B times this. None once a kernel changes after the capture.
+TRAFFIC_BYTES = {"c2": {"gather": None, "spread": None, "pair": None}}
 
 
 def workload(name="c2", n=None, h_ref=None):
@@ -178,6 +181,168 @@ def cpu_baseline(name, target_s=15.0):
             "host_cores": len(os.sched_getaffinity(0))}
 
 
+# The paper's performance study (Section 5.2, Table 3): forces only, a/L = 1/400, eps = 1e-4, Sigma/dx = 1.00,
+# M_G = 10, and per volume fraction the optimal Sigma/sigma and R_c/sigma it reports; its peak was about 7e6
+# particle-applies/s (PTPS) on an RTX 2080 Ti in FP32.
+PAPER_SWEEP = [(0.0005, 5.9, 32.6), (0.002, 5.1, 27.9), (0.008, 3.4, 18.6), (0.032, 1.8, 9.8), (0.128, 1.4, 8.1)]
+PAPER_PEAK_PTPS = 7.0e6
+
+
+def paper_sweep(device, reps=5, warmup=3, full=False):
+    """PTPS of single-system applies on the paper's performance workloads (FP32, forces only). The
+    12.8% row (N = 1.96M; about a minute of host-side RSA placement) runs only with full=True."""
+    import numpy as np
+    import torch
+    from paper_2310_12651_gb300 import fcm, inputs, tune
+    L = 400.0
+    sg = 1.0 / math.sqrt(math.pi)
+    dev = torch.device("cuda", device)
+    stream = torch.cuda.current_stream(dev)
+    rows = []
+    for phi, s_sigma, rc_sigma in PAPER_SWEEP if full else PAPER_SWEEP[:-1]:
+        n = int(round(phi * L ** 3 / (4.0 * math.pi / 3.0)))
+        Sigma = s_sigma * sg
+        M = tune.grid_for(L, Sigma, 1.0)
+        Y = inputs.random_suspension(n, L, 2310127000 + n, min_sep=2.2)
+        F, _ = inputs.random_loads(n, 2310127001 + n, torques=False)
+        pos, Fd = (torch.as_tensor(a, dtype=torch.float32, device=dev) for a in (Y, F))
+        U = torch.empty_like(Fd)
+        p = fcm.make_params(L, M, Sigma, rc_sigma * sg, 10, n, fcm.FCM_FP32)
+        with fcm.Handle(p, device) as h:
+            for _ in range(warmup):
+                h.apply(n, pos, Fd, None, U, None, stream.cuda_stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                h.apply(n, pos, Fd, None, U, None, stream.cuda_stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            # one more apply with per-stage events (not part of the timed loop above)
+            h.set_timing(True)
+            h.read_timing()
+            h.apply(n, pos, Fd, None, U, None, stream.cuda_stream)
+            stages = {k: round(v[0], 4) for k, v in h.read_timing().items() if v[1]}
+            h.set_timing(False)
+            assert h.check() == 0
+        rows.append({"phi": phi, "N": n, "M": M, "Sigma_over_sigma": s_sigma, "R_c_over_sigma": rc_sigma, "M_G": 10,
+                     "ms_per_apply": ms, "ptps": n / (ms * 1e-3), "ratio_to_paper_peak": n / (ms * 1e-3) / PAPER_PEAK_PTPS,
+                     "stage_ms": stages})
+    return {"workload": "paper's Table 3 settings: L = 400a, forces only, eps = 1e-4, Sigma/dx = 1, M_G = 10, "
+                        "optimal Sigma and R_c per phi; one fcm_apply per step, inputs resident, no L2 flush",
+            "paper_peak_ptps": PAPER_PEAK_PTPS, "paper_hardware": "RTX 2080 Ti, FP32", "rows": rows}
+
+
+SERVE_CLASSES = 8          # box-size ladder of the serving mix (log-spaced L, one grid class each)
+SERVE_POOL = 32            # distinct systems drawn for the mix (half spheres, half 64-sphere rods)
+
+
+def serve_pool(seed=2310126900, pool=SERVE_POOL, tol=1e-4):
+    """Systems shaped like the serving mix: N log-uniform in [2e3, 2e5], phi uniform in [0.01, 0.2],
+    half random suspensions (min separation 2a) and half rods of 64 spheres (bond 2.2a, rods may
+    cross). Each box is rounded up to the next of SERVE_CLASSES log-spaced edges between the mix's
+    extremes (34.7a and 437.6a), so requests of one edge share a grid class, whose parameters the
+    autotuner picks for the class's median N at tolerance tol (grids 32^3 to 256^3)."""
+    import numpy as np
+    from paper_2310_12651_gb300 import fcm, inputs, tune
+    rng = np.random.default_rng(seed)
+    lo, hi = inputs.box_edge(2000, 0.2), inputs.box_edge(200000, 0.01)
+    edges = np.exp(np.linspace(np.log(lo), np.log(hi), SERVE_CLASSES))
+    draws = []
+    for k in range(pool):
+        n = int(np.exp(rng.uniform(np.log(2000), np.log(200000))))
+        phi = rng.uniform(0.01, 0.2)
+        rods = k % 2 == 1
+        if rods:
+            n = max(64, 64 * round(n / 64))
+        L = inputs.box_edge(n, phi)
+        c = int(np.searchsorted(edges, L * (1 - 1e-12)))
+        draws.append((n, rods, min(c, SERVE_CLASSES - 1)))
+    classes = {}
+    for c in sorted({d[2] for d in draws}):
+        ns = sorted(d[0] for d in draws if d[2] == c)
+        ch = tune.choose(ns[len(ns) // 2], float(edges[c]), tol, torques=True, max_grid=256, min_grid=32)
+        classes[c] = (float(edges[c]), ch)
+    systems = []
+    for k, (n, rods, c) in enumerate(draws):
+        L, ch = classes[c]
+        if rods:
+            Y, _ = inputs.random_rods(n // 64, 64, L, seed + 10 * k, min_sep=0.0)
+        else:
+            Y = inputs.random_suspension(n, L, seed + 10 * k, min_sep=2.0, max_rounds=400)
+        F, T = inputs.random_loads(n, seed + 10 * k + 1)
+        arrays = tuple(np.ascontiguousarray(a, dtype=np.float32) for a in (Y, F, T))
+        systems.append(dict(n=n, L=L, cls=c, rods=rods, params=tune.make_params(ch, L, n), arrays=arrays))
+    return systems, classes
+
+
+def serve_bench(device, requests=1024, loads=(0.5, 0.9), seed=2310126950):
+    """The serving engine on the mix: capacity with every request queued at once, then Poisson
+    arrivals at fractions of that capacity; latency = submit to completion (host clocks)."""
+    import threading
+    import numpy as np
+    from paper_2310_12651_gb300 import fcm
+    t_gen = time.time()
+    pool, classes = serve_pool()
+    t_gen = time.time() - t_gen
+    rng = np.random.default_rng(seed)
+    order = rng.integers(0, len(pool), size=requests)
+    out = {"pool_systems": len(pool), "grid_classes": len(classes), "requests_per_phase": requests,
+           "classes": [{"L": round(L, 2), "M": ch["M"], "Sigma_over_sigma": ch["Sigma_over_sigma"], "M_G": ch["M_G"],
+                        "r_c": round(ch["r_c"], 2)} for L, ch in classes.values()],
+           "pool_generation_s": round(t_gen, 1), "tolerance": 1e-4}
+    with fcm.Server(device=device, hbm_budget=48 << 30, max_batch=64) as srv:
+        warm = [srv.submit(s["params"], *s["arrays"]) for s in pool]
+        for t in warm:
+            assert srv.wait(t, 120.0) and t.status == fcm.FCM_OK, t.status
+        # capacity: all requests queued at once
+        srv.reset_latency()
+        b0 = srv.stats()
+        t0 = time.perf_counter()
+        tickets = [srv.submit(pool[i]["params"], *pool[i]["arrays"]) for i in order]
+        for t in tickets:
+            assert srv.wait(t, 300.0) and t.status == fcm.FCM_OK
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        particles = int(sum(pool[i]["n"] for i in order))
+        cap_rps = requests / wall
+        out["capacity"] = {"requests_per_s": cap_rps, "particle_applies_per_s": particles / wall,
+                           "p50_ms": st["latency_p50_us"] / 1e3, "p99_ms": st["latency_p99_us"] / 1e3,
+                           "mean_batch": (st["batched_requests"] - b0["batched_requests"]) /
+                                         max(1, st["batches"] - b0["batches"])}
+        out["open_loop"] = []
+        for load in loads:
+            rate = load * cap_rps
+            gaps = rng.exponential(1.0 / rate, size=requests)
+            srv.reset_latency()
+            b0 = srv.stats()
+            tickets = []
+            t0 = time.perf_counter()
+            due = t0
+            for k, i in enumerate(order):
+                due += gaps[k]
+                delay = due - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                tickets.append(srv.submit(pool[i]["params"], *pool[i]["arrays"]))
+            for t in tickets:
+                assert srv.wait(t, 300.0) and t.status == fcm.FCM_OK
+            wall = time.perf_counter() - t0
+            st = srv.stats()
+            out["open_loop"].append({"load": load, "offered_requests_per_s": rate,
+                                     "particle_applies_per_s": particles / wall,
+                                     "p50_ms": st["latency_p50_us"] / 1e3, "p99_ms": st["latency_p99_us"] / 1e3,
+                                     "max_ms": st["latency_max_us"] / 1e3,
+                                     "mean_batch": (st["batched_requests"] - b0["batched_requests"]) /
+                                                   max(1, st["batches"] - b0["batches"])})
+        st = srv.stats()
+        out["handles_created"] = st["handles_created"]
+        out["handles_evicted"] = st["handles_evicted"]
+        out["hbm_bytes"] = st["hbm_bytes"]
+        out["hbm_budget"] = st["hbm_budget"]
+    return out
+
+
 def reference_arm(args, world, rank):
     if rank != 0:
         return 0
@@ -216,6 +381,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--spread-kernel", type=int, default=0, help="0 choose, 1 row-stationary, 2 shared atomics")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving-mix measurement")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the paper-settings PTPS sweep")
+    ap.add_argument("--sweep-full", action="store_true", help="include the 12.8%% (N = 1.96M) sweep row")
+    ap.add_argument("--serve-requests", type=int, default=1024)
+    ap.add_argument("--mode", default="batched", choices=["batched", "single"],
+                    help="batched: one fcm_batch_apply over the stacked systems; single: one fcm_apply per system")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
@@ -238,32 +409,40 @@ def main():
     w = workload(args.workload)
     B = args.batch or WORKLOADS[args.workload]["batch"]
     n = w["n"]
-    params = fcm.make_params(w["L"], w["M"], w["Sigma"], w["r_c"], w["M_G"], n, fcm.FCM_FP32,
+    batched = args.mode == "batched"
+    params = fcm.make_params(w["L"], w["M"], w["Sigma"], w["r_c"], w["M_G"], n * B if batched else n, fcm.FCM_FP32,
                              spread_kernel=args.spread_kernel)
-    h = fcm.Handle(params, local)
-    systems = []
+    h = fcm.Handle(params, local, max_systems=B if batched else 1)
+    Ys, Fs, Ts = [], [], []
     for b in range(B):
         seed = inputs.BASE_SEED + 1 + 100 * b + 10000 * rank
-        Y = inputs.random_suspension(n, w["L"], seed)
+        Ys.append(inputs.random_suspension(n, w["L"], seed))
         F, T = inputs.random_loads(n, seed + 1)
-        systems.append(tuple(torch.as_tensor(a, dtype=torch.float32, device=dev) for a in (Y, F, T)))
-    U = torch.empty((n, 3), dtype=torch.float32, device=dev)
+        Fs.append(F)
+        Ts.append(T)
+    # the B systems stacked along the particle axis: system b owns rows b n .. (b + 1) n - 1
+    pos_all, F_all, T_all = (torch.as_tensor(np.concatenate(a), dtype=torch.float32, device=dev) for a in (Ys, Fs, Ts))
+    offsets = [b * n for b in range(B + 1)]
+    U = torch.empty((n * B, 3), dtype=torch.float32, device=dev)
     W = torch.empty_like(U)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    def apply(b):
-        pos, F, T = systems[b]
-        h.apply(n, pos, F, T, U, W, sptr)
+    def step(pos, F, T):
+        if batched:
+            h.batch_apply(offsets, pos, F, T, U, W, sptr)
+        else:
+            for b in range(B):
+                r = slice(b * n, (b + 1) * n)
+                h.apply(n, pos[r], F[r], T[r], U[r], W[r], sptr)
 
     for k in range(args.warmup):
-        for b in range(B):
-            apply(b)
+        step(pos_all, F_all, T_all)
     torch.cuda.synchronize()
     assert h.check() == 0
 
     # ---- timed region (device time, inputs resident)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(B * args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(B * args.steps)]
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     sampler = ClockSampler(local)
     sampler.start()
     barrier(world)
@@ -271,51 +450,44 @@ def main():
     h.set_timing(True)
     h.read_timing()
     launches0 = h.launch_count()
-    k = 0
-    for s in range(args.steps):
-        for b in range(B):
-            flush.zero_()
-            starts[k].record(stream)
-            apply(b)
-            ends[k].record(stream)
-            k += 1
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        step(pos_all, F_all, T_all)
+        ends[k].record(stream)
     torch.cuda.synchronize()
     barrier(world)
     clocks = sampler.stop()
     launches = h.launch_count() - launches0
     stage = h.read_timing()
     h.set_timing(False)
-    apply_ms = [starts[i].elapsed_time(ends[i]) for i in range(k)]
-    total_ms = max_over_ranks(sum(apply_ms), world, dev)
+    step_ms = [starts[i].elapsed_time(ends[i]) for i in range(args.steps)]
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
     value = world * n * B * args.steps / (total_ms * 1e-3)
     ms_per_step = total_ms / args.steps
 
-    # ---- end to end through host buffers
-    host = []
-    for b in range(min(B, 4)):
-        host.append(tuple(t.cpu().pin_memory() for t in systems[b]))
-    Uh = torch.empty((n, 3), dtype=torch.float32).pin_memory()
+    # ---- end to end through host buffers: pinned host -> device inputs, the pass, device -> host outputs
+    hpos, hF, hT = (t.cpu().pin_memory() for t in (pos_all, F_all, T_all))
+    Uh = torch.empty((n * B, 3), dtype=torch.float32).pin_memory()
     Wh = torch.empty_like(Uh).pin_memory()
-    dpos, dF, dT = (torch.empty((n, 3), dtype=torch.float32, device=dev) for _ in range(3))
+    dpos, dF, dT = (torch.empty((n * B, 3), dtype=torch.float32, device=dev) for _ in range(3))
     e2e_steps = max(1, min(args.steps, 10))
     e2e_ms = 0.0
     for rep in range(args.warmup + e2e_steps):
-        for b in range(B):
-            hp, hF, hT = host[b % len(host)]
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            dpos.copy_(hp, non_blocking=True)
-            dF.copy_(hF, non_blocking=True)
-            dT.copy_(hT, non_blocking=True)
-            h.apply(n, dpos, dF, dT, U, W, sptr)
-            Uh.copy_(U, non_blocking=True)
-            Wh.copy_(W, non_blocking=True)
-            e1.record(stream)
-            e1.synchronize()
-            if rep >= args.warmup:
-                e2e_ms += e0.elapsed_time(e1)
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dpos.copy_(hpos, non_blocking=True)
+        dF.copy_(hF, non_blocking=True)
+        dT.copy_(hT, non_blocking=True)
+        step(dpos, dF, dT)
+        Uh.copy_(U, non_blocking=True)
+        Wh.copy_(W, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if rep >= args.warmup:
+            e2e_ms += e0.elapsed_time(e1)
     e2e_ms = max_over_ranks(e2e_ms, world, dev)
     e2e_value = world * n * B * e2e_steps / (e2e_ms * 1e-3)
 
@@ -323,7 +495,7 @@ def main():
     fp64 = None
     if not args.no_fp64:
         h64 = fcm.Handle(fcm.make_params(w["L"], w["M"], w["Sigma"], w["r_c"], w["M_G"], n, fcm.FCM_FP64), local)
-        pos, F, T = (t.double() for t in systems[0])
+        pos, F, T = (t[:n].double() for t in (pos_all, F_all, T_all))
         U64 = torch.empty((n, 3), dtype=torch.float64, device=dev)
         W64 = torch.empty_like(U64)
         h64.apply(n, pos, F, T, U64, W64, sptr)
@@ -339,10 +511,10 @@ def main():
             e1.record(stream)
             e1.synchronize()
             t64 += e0.elapsed_time(e1)
-        apply(0)
+        step(pos_all, F_all, T_all)
         torch.cuda.synchronize()
-        eu = float(torch.linalg.norm(U.double() - U64) / torch.linalg.norm(U64))
-        ew = float(torch.linalg.norm(W.double() - W64) / torch.linalg.norm(W64))
+        eu = float(torch.linalg.norm(U[:n].double() - U64) / torch.linalg.norm(U64))
+        ew = float(torch.linalg.norm(W[:n].double() - W64) / torch.linalg.norm(W64))
         fp64 = {"value": n * reps / (t64 * 1e-3), "unit": UNIT, "ms_per_apply": t64 / reps,
                 "fp32_rel_l2_vs_fp64": {"U": eu, "W": ew}}
         h64.close()
@@ -352,19 +524,20 @@ def main():
     pk = peaks()
     sm_max = (clocks or {}).get("sm_max_mhz") or pk.get("sm_max_mhz") or 2070.0
     alu_peak = sm_count * 128 * 2 * sm_max * 1e6 / 1e12          # FP32 TFLOP/s, FMA = 2 flops
-    napply = B * args.steps
     avg = {name: (ms / cnt if cnt else None) for name, (ms, cnt) in stage.items()}
-    pts = n * w["M_G"] ** 3
+    per_launch = B if batched else 1        # systems one kernel launch processes
+    pts = per_launch * n * w["M_G"] ** 3
     flops = {"spread": 16.0 * pts, "gather": 16.0 * pts}
     n_nb = n / w["L"] ** 3 * 4.0 / 3.0 * math.pi * w["r_c"] ** 3
-    flops["pair"] = 150.0 * n * n_nb
+    flops["pair"] = 150.0 * per_launch * n * n_nb
     dominant = max(("spread", "gather", "pair"), key=lambda s: avg[s] or 0.0)
     achieved = flops[dominant] / (avg[dominant] * 1e-3) / 1e12
+    traffic = TRAFFIC_BYTES.get(args.workload, {}).get(dominant)
     roofline = {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved / alu_peak, "traffic": TRAFFIC_BYTES.get(args.workload, {}).get(dominant),
+                "frac": achieved / alu_peak, "traffic": traffic * per_launch if traffic else None,
                 "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
                 "flops_per_launch": flops[dominant]}
-    M3 = w["M"] ** 3
+    M3 = per_launch * w["M"] ** 3
     fft_bytes = 72.0 * M3
     hbm = pk.get("hbm_gbs", 6800.0)
     stages_out = {name: {"ms_avg": avg[name], "launches": int(stage[name][1])} for name in stage}
@@ -375,9 +548,14 @@ def main():
         if avg[s_]:
             stages_out[s_]["TFLOPs"] = flops[s_] / (avg[s_] * 1e-3) / 1e12
             stages_out[s_]["frac_alu"] = stages_out[s_]["TFLOPs"] / alu_peak
-            byts = 12.0 * M3 + 48.0 * n
+            byts = 12.0 * M3 + 48.0 * n * per_launch
             stages_out[s_]["GBps"] = byts / (avg[s_] * 1e-3) / 1e9
             stages_out[s_]["frac_hbm"] = stages_out[s_]["GBps"] / hbm
+
+    serve = None
+    if not args.no_serve:
+        serve = serve_bench(local, requests=args.serve_requests)
+    sweep = None if args.no_sweep else paper_sweep(local, full=args.sweep_full)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -387,14 +565,16 @@ def main():
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": describe(w, B), "particles_per_step_per_gpu": n * B,
+                      "mode": ("one batched pass (fcm_batch_apply) over the stacked systems" if batched
+                               else "one fcm_apply per system"),
                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                      "l2": "flushed (256 MB write) before every apply"},
+                      "l2": "flushed (256 MB write) before every step"},
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B * 3 * n * 3 * 4,
                    "d2h_bytes_per_step": B * 2 * n * 3 * 4},
            "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
-           "fp64_plain": fp64,
+           "fp64_plain": fp64, "serve": serve, "paper_sweep": sweep,
            "speedup_vs_fp64_plain": (value / world / fp64["value"]) if fp64 else None,
-           "stages": stages_out, "apply_ms_median": statistics.median(apply_ms),
+           "stages": stages_out, "step_ms_median": statistics.median(step_ms),
            "workspace_bytes": h.workspace_bytes()}
     if rank == 0:
         print(json.dumps(out), flush=True)

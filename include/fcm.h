@@ -24,8 +24,9 @@
  *     [0, L) and are wrapped. Outputs are in input order.
  *   - Every call returns an fcm_status; on failure fcm_last_error() gives a
  *     message (thread-local, valid until the next call on that thread).
- *   - The library allocates all its device workspace in fcm_create and frees it
- *     in fcm_destroy; fcm_apply allocates nothing.
+ *   - The library allocates all its device workspace in fcm_create (or
+ *     fcm_create_batch) and frees it in fcm_destroy; fcm_apply and
+ *     fcm_batch_apply allocate nothing.
  *   - A handle may be used from one host thread at a time. Two calls on
  *     different streams with the same handle race on its workspace.
  */
@@ -46,7 +47,9 @@ typedef enum fcm_status {
   FCM_ERR_CUDA = 3,     /* a CUDA runtime call failed                              */
   FCM_ERR_CUFFT = 4,    /* a cuFFT call failed                                     */
   FCM_ERR_TIMEOUT = 5,  /* a bounded wait ran out                                  */
-  FCM_ERR_INPUT = 6     /* the device flagged bad input (non-finite position)      */
+  FCM_ERR_INPUT = 6,    /* the device flagged bad input (non-finite position)      */
+  FCM_ERR_BUSY = 7,     /* the request is already running (fcm_server_cancel)      */
+  FCM_ERR_CANCELED = 8  /* the request was canceled before it ran                  */
 } fcm_status;
 
 typedef enum fcm_precision {
@@ -116,10 +119,46 @@ enum {
 int fcm_apply_stages(fcm_handle* h, int n, const void* pos, const void* F, const void* T,
                      void* U, void* W, int stages, void* stream);
 
+/* ---- Batched systems (many independent systems in one pass) ----------------
+ * The paper treats one periodic system at a time; running many small systems
+ * one call each leaves the GPU idle between launches. A batch handle holds up
+ * to max_systems systems that share every parameter in p (box, grid, kernel
+ * widths, cutoff, precision), stacked along the particle axis: every stage is
+ * one launch over all systems' tiles, cells and grids, and the FFT is one
+ * batched cuFFT plan. Results equal those of one fcm_apply per system (each
+ * system's arithmetic is unchanged; only the launch covers more of them). */
+#define FCM_MAX_BATCH 1024
+
+/* fcm_create for batches: p->max_n bounds the TOTAL number of particles of one
+ * batch; the grid, spectrum and bins are allocated max_systems times
+ * (1 <= max_systems <= FCM_MAX_BATCH). FP64 handles hold one grid and run a
+ * batch one system after another. fcm_create(p, d, out) is
+ * fcm_create_batch(p, 1, d, out). Synchronous. */
+int fcm_create_batch(const fcm_params* p, int max_systems, int device, fcm_handle** out);
+
+/* (U, W) = M (F, T) for n_sys independent systems (0 <= n_sys <= max_systems).
+ *   offsets : HOST array of n_sys + 1 ints [read during the call only]:
+ *             offsets[0] = 0, nondecreasing, offsets[n_sys] <= max_n; system s
+ *             owns rows offsets[s] .. offsets[s+1]-1 of every particle array
+ *   pos, F, T, U, W : stacked (offsets[n_sys], 3) arrays, as for fcm_apply
+ * Systems do not interact: each sees only its own particles and its own
+ * periodic images. Empty systems are allowed. Bad offsets give FCM_ERR_ARG
+ * before any work is enqueued. Asynchronous on `stream`. */
+int fcm_batch_apply(fcm_handle* h, int n_sys, const int* offsets, const void* pos, const void* F,
+                    const void* T, void* U, void* W, void* stream);
+
+/* fcm_batch_apply restricted to `stages` (FCM_STAGE_GRID, FCM_STAGE_PAIR). */
+int fcm_batch_apply_stages(fcm_handle* h, int n_sys, const int* offsets, const void* pos, const void* F,
+                           const void* T, void* U, void* W, int stages, void* stream);
+
+/* max_systems of the handle (1 for fcm_create), 0 for NULL. */
+int fcm_max_systems(const fcm_handle* h);
+
 /* Copies the handle's real grid (3 components, layout [c][z][y][x], x fastest,
  * M_x*M_y*M_z values per component, the handle's precision) to device memory
  * `dst`. After fcm_apply_stages(FCM_STAGE_GRID) it holds the grid velocity u;
- * after fcm_spread it holds the spread force density f. */
+ * after fcm_spread it holds the spread force density f. A batch handle copies
+ * the grid of system 0. */
 int fcm_copy_grid(fcm_handle* h, void* dst, void* stream);
 
 /* Sort and spread only: afterwards the grid holds f (Section 4, steps 1-3). */
@@ -156,6 +195,77 @@ size_t fcm_workspace_bytes(const fcm_handle* h);
  * 1/(8 pi eta a^3) and WF relative to their geometric mean). Host only. */
 int fcm_cutoff_radius(double Sigma, double Sigma_D, double a, double eta, double tol,
                       int torques, double* r_c);
+
+/* ---- Serving engine --------------------------------------------------------
+ * A request queue in front of the batched path, for many independent systems
+ * of mixed sizes and boxes submitted from any host threads. The paper has no
+ * counterpart; each request is computed exactly as fcm_apply would compute it.
+ *   - Requests whose parameters agree (box, grid, Sigma, Sigma_D, r_c, M_G, a,
+ *     eta, precision, and whether torques act: a "grid class") and that wait at
+ *     the same time run as one fcm_batch_apply pass (up to max_batch systems).
+ *   - Batch handles are cached per grid class and capacity, so repeated classes
+ *     neither allocate nor plan. The device bytes of cached handles and staging
+ *     stay within hbm_budget: idle handles are evicted least recently used
+ *     first; a request whose handle alone would exceed it fails with
+ *     FCM_ERR_OOM (admission control).
+ *   - Two launch slots (own stream, pinned staging) overlap one pass's copies
+ *     and kernels with the next pass's.
+ *   - One worker thread issues all GPU work; submit/poll/cancel/stats may be
+ *     called from any thread, fcm_server_destroy from one thread after all
+ *     other calls have returned. */
+typedef struct fcm_server fcm_server;
+
+typedef struct fcm_request {
+  fcm_params params;  /* the system; max_n, tile and spread_kernel are ignored        */
+  int n;              /* particles, >= 0                                              */
+  const void* pos;    /* HOST (n, 3) positions, params.precision                      */
+  const void* F;      /* HOST (n, 3) forces                                           */
+  const void* T;      /* HOST (n, 3) torques, or NULL                                 */
+  void* U;            /* HOST (n, 3) velocities                                       */
+  void* W;            /* HOST (n, 3) angular velocities, or NULL                      */
+} fcm_request;        /* the caller keeps all five arrays alive until the request is  */
+                      /* done; inputs are read when it launches, outputs written      */
+                      /* before it completes                                          */
+
+typedef struct fcm_server_stats {
+  long long submitted, completed, rejected, canceled, failed, pending;
+  long long batches;           /* passes launched                                    */
+  long long batched_requests;  /* requests those passes carried                      */
+  long long handles_created, handles_evicted;
+  size_t hbm_bytes;            /* device bytes held by cached handles and staging    */
+  size_t hbm_budget;
+  double latency_p50_us, latency_p99_us, latency_max_us;  /* submit to completion,  */
+                                                           /* last 131072 requests  */
+} fcm_server_stats;
+
+/* Starts a server on `device` (worker thread, two streams). hbm_budget > 0 bytes;
+ * 1 <= max_batch <= FCM_MAX_BATCH systems per pass. */
+int fcm_server_create(int device, size_t hbm_budget, int max_batch, fcm_server** out);
+
+/* Queues a request; returns at once with its id. Parameters are checked as
+ * fcm_create checks them: an invalid request returns FCM_ERR_ARG and is not
+ * queued. n == 0 completes immediately. */
+int fcm_server_submit(fcm_server* s, const fcm_request* r, long long* id);
+
+/* Waits up to timeout_us (0: no wait) for request `id`. Returns FCM_OK once it
+ * is done, with *status its result (FCM_OK, FCM_ERR_OOM when the budget
+ * refused it, FCM_ERR_CANCELED, FCM_ERR_CUDA ...), and forgets the id;
+ * FCM_ERR_TIMEOUT if it is still queued or running; FCM_ERR_ARG for an
+ * unknown id. */
+int fcm_server_poll(fcm_server* s, long long id, long long timeout_us, int* status);
+
+/* Removes a request that has not launched yet (it completes with
+ * FCM_ERR_CANCELED); FCM_ERR_BUSY if it already launched or finished. */
+int fcm_server_cancel(fcm_server* s, long long id);
+
+/* Counters, HBM use and latency percentiles. */
+int fcm_server_get_stats(fcm_server* s, fcm_server_stats* out);
+
+/* Clears the latency window (counters are kept). */
+int fcm_server_reset_latency(fcm_server* s);
+
+/* Cancels queued requests, waits for passes in flight, frees everything. */
+int fcm_server_destroy(fcm_server* s);
 
 /* Capacity of fcm_pair_correction_noalloc's fixed scratch. */
 #define FCM_NOALLOC_MAX_N 65536

@@ -11,11 +11,23 @@
 
 namespace fcm {
 
+// System of stacked row i: the s with sys_off[s] <= i < sys_off[s + 1] (binary search).
+__device__ inline int system_of(const BinBuffers& b, int i) {
+  if (b.nsys <= 1 || !b.sys_off) return 0;
+  int lo = 0, hi = b.nsys - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(b.sys_off + mid) <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256) key_count_kernel(Geometry<R> g, int n, const R* __restrict__ pos,
                                                         BinBuffers b, int need_cells) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const int sys = system_of(b, i);
   int bad = 0;
   int t[3], c[3];
 #pragma unroll
@@ -27,17 +39,20 @@ __global__ void __launch_bounds__(256) key_count_kernel(Geometry<R> g, int n, co
   }
   if (bad) atomicOr(b.status, kStatusNonFinite);
   unsigned tk = (unsigned)(t[0] + g.ntile[0] * (t[1] + g.ntile[1] * t[2]));
+  if (sys) tk += (unsigned)sys * (unsigned)g.tiles_per;
   b.tile_key[i] = tk;
   b.tile_rank[i] = (unsigned)atomicAdd(&b.tile_count[tk], 1);
   if (need_cells) {
     unsigned ck = (unsigned)(c[0] + g.mcell[0] * (c[1] + g.mcell[1] * c[2]));
+    if (sys) ck += (unsigned)sys * (unsigned)g.cells_per;
     b.cell_key[i] = ck;
     b.cell_rank[i] = (unsigned)atomicAdd(&b.cell_count[ck], 1);
   }
 }
 
-// Exclusive scan of one counter array by one block; start[nb] = total. Resets counts.
-__device__ void block_scan(int* count, int* start, int nb) {
+// Exclusive scan of one counter array by one block, offset by base; start[nb] = base + total
+// when write_end. Resets counts.
+__device__ void block_scan(int* count, int* start, int nb, int base, bool write_end) {
   __shared__ int warp_sums[32];
   __shared__ int carry;
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -67,19 +82,31 @@ __device__ void block_scan(int* count, int* start, int nb) {
     if (lane == nw - 1) carry = w;
   }
   __syncthreads();
-  int excl = v - local + (wid > 0 ? warp_sums[wid - 1] : 0);
+  int excl = base + v - local + (wid > 0 ? warp_sums[wid - 1] : 0);
   for (int k = lo; k < hi; ++k) {
     int cnt = count[k];
     start[k] = excl;
     excl += cnt;
     count[k] = 0;
   }
-  if (tid == 0) start[nb] = carry;
+  if (tid == 0 && write_end) start[nb] = base + carry;
 }
 
+// Block (k, s): k = 0 scans system s's tile counters, k = 1 its cell counters. A system's
+// bins are contiguous and its particles are the stacked rows from sys_off[s], so each
+// segment starts at sys_off[s] and the segments scan independently.
 __global__ void __launch_bounds__(1024) scan_kernel(BinBuffers b, int need_cells) {
-  if (blockIdx.x == 0) block_scan(b.tile_count, b.tile_start, b.ntiles);
-  else if (need_cells) block_scan(b.cell_count, b.cell_start, b.ncells);
+  const int sys = blockIdx.y;
+  const int nsys = max(b.nsys, 1);
+  const int base = (b.nsys > 1 && b.sys_off) ? b.sys_off[sys] : 0;
+  const bool last = sys == nsys - 1;
+  if (blockIdx.x == 0) {
+    const int per = b.ntiles / nsys;
+    block_scan(b.tile_count + (size_t)sys * per, b.tile_start + (size_t)sys * per, per, base, last);
+  } else if (need_cells) {
+    const int per = b.ncells / nsys;
+    block_scan(b.cell_count + (size_t)sys * per, b.cell_start + (size_t)sys * per, per, base, last);
+  }
 }
 
 template <typename R>
@@ -119,7 +146,7 @@ void launch_binning(const Geometry<R>& g, int n, const R* pos, const R* F, const
   if (n <= 0) return;
   int blocks = (n + 255) / 256;
   key_count_kernel<R><<<blocks, 256, 0, s>>>(g, n, pos, b, need_cells ? 1 : 0);
-  scan_kernel<<<2, 1024, 0, s>>>(b, need_cells ? 1 : 0);
+  scan_kernel<<<dim3(2, b.nsys > 1 ? b.nsys : 1), 1024, 0, s>>>(b, need_cells ? 1 : 0);
   scatter_kernel<R><<<blocks, 256, 0, s>>>(g, n, pos, F, T, b, need_cells ? 1 : 0);
   *launches += 3;
 }
@@ -128,6 +155,40 @@ template void launch_binning<float>(const Geometry<float>&, int, const float*, c
                                     const BinBuffers&, bool, cudaStream_t, long long*);
 template void launch_binning<double>(const Geometry<double>&, int, const double*, const double*, const double*,
                                      const BinBuffers&, bool, cudaStream_t, long long*);
+
+__global__ void write_offsets_kernel(SysOffsets o, int n, int* dst) {
+  for (int k = threadIdx.x; k <= n; k += blockDim.x) dst[k] = o.off[k];
+}
+
+void launch_write_offsets(const SysOffsets& o, int n, int* dst, cudaStream_t s, long long* launches) {
+  write_offsets_kernel<<<1, 256, 0, s>>>(o, n, dst);
+  *launches += 1;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) add_kernel(R* __restrict__ U, const R* __restrict__ up, R* __restrict__ W,
+                                                  const R* __restrict__ wp, size_t count) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < count; k += stride) {
+    U[k] += up[k];
+    if (W) W[k] += wp[k];
+  }
+}
+
+template <typename R>
+void launch_add(R* U, const R* up, R* W, const R* wp, size_t count, cudaStream_t s, long long* launches) {
+  if (count == 0) return;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t want = (count + 255) / 256;
+  const int blocks = (int)(want < (size_t)sms * 8 ? want : (size_t)sms * 8);
+  add_kernel<R><<<blocks, 256, 0, s>>>(U, up, W, wp, count);
+  *launches += 1;
+}
+
+template void launch_add<float>(float*, const float*, float*, const float*, size_t, cudaStream_t, long long*);
+template void launch_add<double>(double*, const double*, double*, const double*, size_t, cudaStream_t, long long*);
 
 __global__ void zero_kernel(uint4* p, size_t n16, unsigned char* tail, size_t ntail) {
   size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;

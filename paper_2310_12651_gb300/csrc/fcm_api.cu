@@ -1,15 +1,17 @@
 // libfcm C-ABI: handle lifetime, parameter checks, workspace, and the launch
 // sequence of one mobility product (Section 4):
 //
-//   caller stream : bin ─► zero grid ─► spread ─┬─► R2C ─► project ─► C2R ─┐
-//                                               └─(event)─► side: pair ─(event)─┴► gather (+ pair sums) ─► U, W
+//   caller stream : bin ─► zero grid ─► spread ─┬─► R2C ─► project ─► C2R ─► gather ─┬─► add ─► U, W
+//                                               └─(event)─► side: pair ───(event)───┘
 //
 // The pair correction only needs the cell-sorted particles. It is forked onto
 // the handle's side stream after the spread, where it overlaps the
-// latency-bound FFT chain (spread and pair both fill the GPU, so overlapping
-// them gains nothing); the gather kernel adds the pair sums when it writes U
-// and W in input order. The fork/join uses events
-// only, so a caller may capture fcm_apply into a CUDA graph.
+// latency-bound FFT chain and the gather (the spread fills every SM's
+// registers, so overlapping it gains nothing; a gather CTA leaves room for a
+// pair CTA on the same SM). The gather writes the grid part of U and W in
+// input order, the pair kernel its sums, and a small kernel adds them after
+// the join. The fork/join uses events only, so a caller may capture fcm_apply
+// into a CUDA graph.
 #include <cufft.h>
 
 #include <chrono>
@@ -17,6 +19,7 @@
 #include <cstring>
 #include <string>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/fcm.h"
@@ -217,8 +220,13 @@ struct fcm_handle {
   void* wpair = nullptr;
   void* wscratch = nullptr;
   size_t grid_bytes = 0;
-  cufftHandle r2c = 0, c2r = 0;
-  bool plans = false;
+  // FFT plans per batch bucket (1, 2, 4, ... systems, and max_systems), sharing one work area
+  struct Plan { int systems; cufftHandle r2c, c2r; };
+  std::vector<Plan> plans;
+  void* fft_work = nullptr;
+  int max_systems = 1;
+  int* sys_off = nullptr;       // device offsets of the current batched pass
+  size_t spec_bytes = 0;        // one system's spectra
   size_t bytes = 0;
   long long launches = 0;
   std::vector<void*> allocs;
@@ -251,9 +259,9 @@ void release(fcm_handle* h) {
   if (!h) return;
   cudaSetDevice(h->device);
   cudaDeviceSynchronize();
-  if (h->plans) {
-    cufftDestroy(h->r2c);
-    cufftDestroy(h->c2r);
+  for (auto& pl : h->plans) {
+    cufftDestroy(pl.r2c);
+    cufftDestroy(pl.c2r);
   }
   for (auto& ev : h->pool) {
     cudaEventDestroy(ev.a);
@@ -299,8 +307,21 @@ void choose_tile(const fcm_params& p, int tile[3]) {
   tile[0] = tile[1] = tile[2] = 1;
 }
 
+// Pair cells: side max(r_c, s_occ) with s_occ = (kCellTarget / rho)^(1/3), rho the capacity's number
+// density (max_n particles over `systems` boxes). Any side >= r_c keeps every pair within the 27
+// neighbouring cells (Section 4 step 1 uses side r_c); in dilute systems an r_c cell holds about one
+// particle, and a CTA per cell would then stage 27 cells for a single particle.
+constexpr double kCellTarget = 8.0;
+
+double cell_side(const fcm_params& p, int systems) {
+  const double V = p.L[0] * p.L[1] * p.L[2];
+  const double rho = (double)std::max(p.max_n, 1) / ((double)std::max(systems, 1) * V);
+  return std::max(p.r_c, std::cbrt(kCellTarget / rho));
+}
+
 template <typename R>
-void fill_geometry(const fcm_params& p, const int tile[3], Geometry<R>* g) {
+void fill_geometry(const fcm_params& p, const int tile[3], Geometry<R>* g, int systems = 1) {
+  const double side = (p.r_c > 0) ? cell_side(p, systems) : 0.0;
   for (int d = 0; d < 3; ++d) {
     g->L[d] = (R)p.L[d];
     g->h[d] = (R)(p.L[d] / p.M[d]);
@@ -308,13 +329,17 @@ void fill_geometry(const fcm_params& p, const int tile[3], Geometry<R>* g) {
     g->M[d] = p.M[d];
     g->tile[d] = tile[d];
     g->ntile[d] = (p.M[d] + tile[d] - 1) / tile[d];
-    // cells per dimension max(int(L/r_c), 3), clamped before the integer conversion
-    const double m = (p.r_c > 0) ? std::floor(p.L[d] / p.r_c) : 3.0;
+    // cells per dimension max(int(L/side), 3), clamped before the integer conversion
+    const double m = (p.r_c > 0) ? std::floor(p.L[d] / side) : 3.0;
     g->mcell[d] = (int)std::min(std::max(m, 3.0), 1048576.0);
     g->cellw_inv[d] = (R)(g->mcell[d] / p.L[d]);
   }
   g->shift = (g->mcell[0] >= 4 && g->mcell[1] >= 4 && g->mcell[2] >= 4) ? 1 : 0;
   g->MG = p.M_G;
+  g->nsys = 1;
+  g->tiles_per = g->ntile[0] * g->ntile[1] * g->ntile[2];
+  g->cells_per = g->mcell[0] * g->mcell[1] * g->mcell[2];
+  g->grid_stride = 3LL * p.M[0] * p.M[1] * p.M[2];
 }
 
 template <typename R>
@@ -393,79 +418,100 @@ int stage_end(fcm_handle* h, int slot, cudaStream_t s) {
 // Forks the pair correction onto the side stream (it needs only the cell-sorted
 // particles); the caller joins on ev_join before the gather.
 template <typename R>
-int launch_pair_stage(fcm_handle* h, int n, R* U, R* Wout, bool torque, bool grid_on, cudaStream_t s) {
+int launch_pair_stage(fcm_handle* h, const Geometry<R>& g, const BinBuffers& bb, int n, R* U, R* Wout, bool torque,
+                      bool grid_on, cudaStream_t s) {
   int rc, t_pair;
   R* up = grid_on ? (R*)h->upair : U;
   R* wp = grid_on ? (R*)h->wpair : Wout;
   FCM_CUDA(cudaEventRecord(h->ev_fork, s));
   FCM_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
   if ((rc = stage_begin(h, 4, h->side, &t_pair))) return rc;
-  if (h->fp64)
-    launch_pair_f64(h->gd, h->pd, torque, h->bb, n, (double*)up, (double*)wp, h->side, &h->launches);
+  if constexpr (std::is_same<R, double>::value)
+    launch_pair_f64(g, h->pd, torque, bb, n, up, wp, h->side, &h->launches);
   else
-    launch_pair_f32(h->gf, h->pf, h->ptab, torque, h->bb, n, (float*)up, (float*)wp, h->side, &h->launches);
+    launch_pair_f32(g, h->pf, h->ptab, torque, bb, n, up, wp, h->side, &h->launches);
   if ((rc = stage_end(h, t_pair, h->side))) return rc;
   FCM_CUDA(cudaGetLastError());
   FCM_CUDA(cudaEventRecord(h->ev_join, h->side));
   return FCM_OK;
 }
 
+const fcm_handle::Plan* plan_for(const fcm_handle* h, int nsys) {
+  for (const auto& pl : h->plans)
+    if (pl.systems >= nsys) return &pl;
+  return nullptr;
+}
+
+// One pass over nsys stacked systems (nsys > 1 only on the FP32 path; h->sys_off then holds
+// the offsets). Plans cover a bucket of systems >= nsys: the bucket's extra grids are zeroed
+// with the others, so their transforms stay zero.
 template <typename R>
-int run(fcm_handle* h, int n, const R* pos, const R* F, const R* T, R* U, R* W, int stages, bool spread_only,
-        cudaStream_t s) {
+int run(fcm_handle* h, int nsys, int n, const R* pos, const R* F, const R* T, R* U, R* W, int stages,
+        bool spread_only, cudaStream_t s) {
   const bool torque = (T != nullptr) || (W != nullptr);
   R* Wout = W ? W : (torque ? (R*)h->wscratch : nullptr);
   const bool grid_on = spread_only || (stages & FCM_STAGE_GRID);
   const bool pair_on = !spread_only && (stages & FCM_STAGE_PAIR) && h->pairs_on;
-  const Geometry<R>& g = *reinterpret_cast<const Geometry<R>*>(h->fp64 ? (const void*)&h->gd : (const void*)&h->gf);
+  Geometry<R> g = *reinterpret_cast<const Geometry<R>*>(h->fp64 ? (const void*)&h->gd : (const void*)&h->gf);
+  BinBuffers bb = h->bb;
+  const fcm_handle::Plan* plan = plan_for(h, nsys);
+  if (!plan) return fail(FCM_ERR_ARG, "no FFT plan for " + std::to_string(nsys) + " systems");
+  g.nsys = nsys;
+  bb.nsys = nsys;
+  bb.sys_off = nsys > 1 ? h->sys_off : nullptr;
+  bb.ntiles = nsys * g.tiles_per;
+  bb.ncells = pair_on ? nsys * g.cells_per : bb.ncells;
   int rc, t_all, t_bin, t_spread, t_fft, t_gather;
   if ((rc = stage_begin(h, 5, s, &t_all))) return rc;
   if ((rc = stage_begin(h, 0, s, &t_bin))) return rc;
-  launch_binning<R>(g, n, pos, F, T, h->bb, pair_on, s, &h->launches);
+  launch_binning<R>(g, n, pos, F, T, bb, pair_on, s, &h->launches);
   if ((rc = stage_end(h, t_bin, s))) return rc;
   FCM_CUDA(cudaGetLastError());
   if (grid_on) {
-    launch_zero(h->grid, h->grid_bytes, s, &h->launches);
+    launch_zero(h->grid, h->grid_bytes * plan->systems, s, &h->launches);
     if ((rc = stage_begin(h, 1, s, &t_spread))) return rc;
-    if (h->fp64)
-      launch_spread_f64(h->gd, h->kd, torque, h->bb, n, (double*)h->grid, s, &h->launches);
+    if constexpr (std::is_same<R, double>::value)
+      launch_spread_f64(g, h->kd, torque, bb, n, (double*)h->grid, s, &h->launches);
     else
-      launch_spread_f32(h->gf, h->kf, torque, h->p.spread_kernel, h->bb, (float*)h->grid, s, &h->launches);
+      launch_spread_f32(g, h->kf, torque, h->p.spread_kernel, bb, (float*)h->grid, s, &h->launches);
     if ((rc = stage_end(h, t_spread, s))) return rc;
     FCM_CUDA(cudaGetLastError());
     if (pair_on && !spread_only) {
-      if ((rc = launch_pair_stage(h, n, U, Wout, torque, grid_on, s))) return rc;
+      if ((rc = launch_pair_stage(h, g, bb, n, U, Wout, torque, grid_on, s))) return rc;
     }
     if (!spread_only) {
       if ((rc = stage_begin(h, 2, s, &t_fft))) return rc;
-      FCM_CUFFT(cufftSetStream(h->r2c, s));
-      FCM_CUFFT(cufftSetStream(h->c2r, s));
-      if (h->fp64) {
-        FCM_CUFFT(cufftExecD2Z(h->r2c, (cufftDoubleReal*)h->grid, (cufftDoubleComplex*)h->spec));
-        launch_projection<double>(h->gd, h->p.eta, h->spec, s, &h->launches);
-        FCM_CUFFT(cufftExecZ2D(h->c2r, (cufftDoubleComplex*)h->spec, (cufftDoubleReal*)h->grid));
+      FCM_CUFFT(cufftSetStream(plan->r2c, s));
+      FCM_CUFFT(cufftSetStream(plan->c2r, s));
+      if constexpr (std::is_same<R, double>::value) {
+        FCM_CUFFT(cufftExecD2Z(plan->r2c, (cufftDoubleReal*)h->grid, (cufftDoubleComplex*)h->spec));
+        launch_projection<double>(g, h->p.eta, h->spec, s, &h->launches);
+        FCM_CUFFT(cufftExecZ2D(plan->c2r, (cufftDoubleComplex*)h->spec, (cufftDoubleReal*)h->grid));
       } else {
-        FCM_CUFFT(cufftExecR2C(h->r2c, (cufftReal*)h->grid, (cufftComplex*)h->spec));
-        launch_projection<float>(h->gf, (float)h->p.eta, h->spec, s, &h->launches);
-        FCM_CUFFT(cufftExecC2R(h->c2r, (cufftComplex*)h->spec, (cufftReal*)h->grid));
+        FCM_CUFFT(cufftExecR2C(plan->r2c, (cufftReal*)h->grid, (cufftComplex*)h->spec));
+        launch_projection<float>(g, (float)h->p.eta, h->spec, s, &h->launches);
+        FCM_CUFFT(cufftExecC2R(plan->c2r, (cufftComplex*)h->spec, (cufftReal*)h->grid));
       }
       if ((rc = stage_end(h, t_fft, s))) return rc;
       FCM_CUDA(cudaGetLastError());
-      if (pair_on) FCM_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
+      // the gather writes the grid part; the pair sums, which run beside the FFT and the gather,
+      // are added once both are done
       if ((rc = stage_begin(h, 3, s, &t_gather))) return rc;
-      const R* up = pair_on ? (const R*)h->upair : nullptr;
-      const R* wp = pair_on ? (const R*)h->wpair : nullptr;
-      if (h->fp64)
-        launch_gather_f64(h->gd, h->kd, torque, h->bb, n, (const double*)h->grid, (const double*)up,
-                          (const double*)wp, (double*)U, (double*)Wout, s, &h->launches);
+      if constexpr (std::is_same<R, double>::value)
+        launch_gather_f64(g, h->kd, torque, bb, n, (const double*)h->grid, nullptr, nullptr, U, Wout, s,
+                          &h->launches);
       else
-        launch_gather_f32(h->gf, h->kf, torque, h->bb, (const float*)h->grid, (const float*)up,
-                          (const float*)wp, (float*)U, (float*)Wout, s, &h->launches);
+        launch_gather_f32(g, h->kf, torque, bb, (const float*)h->grid, nullptr, nullptr, U, Wout, s, &h->launches);
       if ((rc = stage_end(h, t_gather, s))) return rc;
       FCM_CUDA(cudaGetLastError());
+      if (pair_on) {
+        FCM_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
+        launch_add<R>(U, (const R*)h->upair, Wout, (const R*)h->wpair, 3 * (size_t)n, s, &h->launches);
+        FCM_CUDA(cudaGetLastError());
+      }
     }
   } else if (pair_on) {
-    if ((rc = launch_pair_stage(h, n, U, Wout, torque, grid_on, s))) return rc;
+    if ((rc = launch_pair_stage(h, g, bb, n, U, Wout, torque, grid_on, s))) return rc;
     FCM_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
   } else if (!spread_only) {  // only the correction requested and it is identically zero
     launch_zero(U, sizeof(R) * 3 * (size_t)n, s, &h->launches);
@@ -488,13 +534,102 @@ int apply_common(fcm_handle* h, int n, const void* pos, const void* F, const voi
   DeviceGuard guard(h->device);
   cudaStream_t s = (cudaStream_t)stream;
   if (h->fp64)
-    return run<double>(h, n, (const double*)pos, (const double*)F, (const double*)T, (double*)U, (double*)W,
+    return run<double>(h, 1, n, (const double*)pos, (const double*)F, (const double*)T, (double*)U, (double*)W,
                        stages, spread_only, s);
-  return run<float>(h, n, (const float*)pos, (const float*)F, (const float*)T, (float*)U, (float*)W, stages,
+  return run<float>(h, 1, n, (const float*)pos, (const float*)F, (const float*)T, (float*)U, (float*)W, stages,
                     spread_only, s);
 }
 
+// Stacked systems: FP32 runs them as one pass; the FP64 plain path runs them one after another.
+int batch_common(fcm_handle* h, int nsys, const int* offsets, const void* pos, const void* F, const void* T,
+                 void* U, void* W, int stages, void* stream) {
+  if (!h) return fail(FCM_ERR_ARG, "handle is NULL");
+  if (nsys < 0 || nsys > h->max_systems)
+    return fail(FCM_ERR_ARG, "n_sys = " + std::to_string(nsys) + " outside [0, max_systems = " +
+                                 std::to_string(h->max_systems) + "]");
+  if (nsys == 0) return FCM_OK;
+  if (!offsets) return fail(FCM_ERR_ARG, "offsets is NULL");
+  if (offsets[0] != 0) return fail(FCM_ERR_ARG, "offsets[0] must be 0");
+  for (int k = 0; k < nsys; ++k)
+    if (offsets[k + 1] < offsets[k]) return fail(FCM_ERR_ARG, "offsets must be nondecreasing");
+  const int n = offsets[nsys];
+  if (n > h->p.max_n)
+    return fail(FCM_ERR_ARG, "offsets[n_sys] = " + std::to_string(n) + " exceeds max_n = " + std::to_string(h->p.max_n));
+  if (n > 0 && (!pos || !F || !U)) return fail(FCM_ERR_ARG, "pos, F and U must be non-NULL when particles are present");
+  if (stages < 1 || stages > FCM_STAGE_ALL) return fail(FCM_ERR_ARG, "stages must be a non-empty subset of FCM_STAGE_ALL");
+  if (n == 0) return FCM_OK;
+  DeviceGuard guard(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (h->fp64) {
+    for (int k = 0; k < nsys; ++k) {
+      const int nk = offsets[k + 1] - offsets[k];
+      if (nk == 0) continue;
+      const size_t o = 3 * (size_t)offsets[k];
+      int rc = run<double>(h, 1, nk, (const double*)pos + o, (const double*)F + o, T ? (const double*)T + o : nullptr,
+                           (double*)U + o, W ? (double*)W + o : nullptr, stages, false, s);
+      if (rc) return rc;
+    }
+    return FCM_OK;
+  }
+  if (nsys > 1) {
+    SysOffsets so;
+    for (int k = 0; k <= nsys; ++k) so.off[k] = offsets[k];
+    launch_write_offsets(so, nsys, h->sys_off, s, &h->launches);
+  }
+  return run<float>(h, nsys, n, (const float*)pos, (const float*)F, (const float*)T, (float*)U, (float*)W, stages,
+                    false, s);
+}
+
 }  // namespace
+
+namespace fcm {
+
+// Host checks of fcm_create (without touching a device): parameter ranges and the cutoff rule.
+int check_params(const fcm_params* p, std::string* why) {
+  if (!p) { *why = "params is NULL"; return 0; }
+  if (!validate(p, why)) return 0;
+  const double sg = p->a / std::sqrt(kPi), sD = p->a / std::cbrt(6.0 * std::sqrt(kPi));
+  const double SigmaD = (p->Sigma_D == 0.0) ? p->Sigma : p->Sigma_D;
+  const bool pairs_on = (p->Sigma > sg * (1 + 1e-12)) || (SigmaD > sD * (1 + 1e-12));
+  if (pairs_on) {
+    const double Lmin = std::min(p->L[0], std::min(p->L[1], p->L[2]));
+    if (!(p->r_c > 0) || !(p->r_c <= 0.5 * Lmin)) { *why = "r_c must satisfy 0 < r_c <= min(L)/2"; return 0; }
+    double cells = 1.0;
+    for (int d = 0; d < 3; ++d) cells *= std::min(std::max(std::floor(p->L[d] / p->r_c), 3.0), 1048576.0);
+    if (cells > (double)(1u << 26)) { *why = "too many pair cells (r_c too small for L)"; return 0; }
+  }
+  return 1;
+}
+
+// Device bytes fcm_create_batch(p, max_systems) would allocate (cuFFT work area estimated by cuFFT).
+size_t workspace_estimate(const fcm_params& p, int max_systems) {
+  const bool fp64 = p.precision == FCM_FP64;
+  const int gsys = fp64 ? 1 : max_systems;
+  int tile[3];
+  if (fp64) { tile[0] = tile[1] = tile[2] = std::min(8, std::min(p.M[0], std::min(p.M[1], p.M[2]))); }
+  else choose_tile(p, tile);
+  Geometry<double> g{};
+  fill_geometry(p, tile, &g, max_systems);
+  const size_t n = (size_t)std::max(p.max_n, 1);
+  const size_t rsz = fp64 ? sizeof(double) : sizeof(float);
+  const size_t v4 = fp64 ? sizeof(Vec4<double>) : sizeof(Vec4<float>);
+  const size_t mtot = (size_t)p.M[0] * p.M[1] * p.M[2];
+  const size_t ncplx = (size_t)(p.M[0] / 2 + 1) * p.M[1] * p.M[2];
+  const size_t ntiles = (size_t)g.tiles_per * gsys, ncells = (size_t)g.cells_per * gsys;
+  size_t b = 16 * n + 8 * (ntiles + 1) + 8 * (ncells + 1) + 6 * v4 * n + 256 + 4 * (kMaxBatch + 1) + 9 * rsz * n;
+  b += (3 * rsz * mtot + 6 * rsz * ncplx) * gsys + sizeof(float4) * 5 * kPairTableIntervals;
+  int dims[3] = {p.M[2], p.M[1], p.M[0]};
+  size_t w1 = 0, w2 = 0;
+  if (cufftEstimateMany(3, dims, nullptr, 1, (int)mtot, nullptr, 1, (int)ncplx, fp64 ? CUFFT_D2Z : CUFFT_R2C,
+                        3 * gsys, &w1) != CUFFT_SUCCESS)
+    w1 = 6 * rsz * ncplx * gsys;
+  if (cufftEstimateMany(3, dims, nullptr, 1, (int)ncplx, nullptr, 1, (int)mtot, fp64 ? CUFFT_Z2D : CUFFT_C2R,
+                        3 * gsys, &w2) != CUFFT_SUCCESS)
+    w2 = w1;
+  return b + std::max(w1, w2) + 24 * 256;
+}
+
+}  // namespace fcm
 
 #pragma GCC visibility push(default)
 extern "C" {
@@ -510,12 +645,16 @@ int fcm_params_default(fcm_params* p) {
   return FCM_OK;
 }
 
-int fcm_create(const fcm_params* p, int device, fcm_handle** out) {
+int fcm_create(const fcm_params* p, int device, fcm_handle** out) { return fcm_create_batch(p, 1, device, out); }
+
+int fcm_create_batch(const fcm_params* p, int max_systems, int device, fcm_handle** out) {
   if (!out) return fail(FCM_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (!p) return fail(FCM_ERR_ARG, "params is NULL");
+  if (max_systems < 1 || max_systems > FCM_MAX_BATCH)
+    return fail(FCM_ERR_ARG, "max_systems must be in [1, " + std::to_string(FCM_MAX_BATCH) + "]");
   std::string why;
-  if (!validate(p, &why)) return fail(FCM_ERR_ARG, why);
+  if (!check_params(p, &why)) return fail(FCM_ERR_ARG, why);
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
     cudaGetLastError();
@@ -534,13 +673,15 @@ int fcm_create(const fcm_params* p, int device, fcm_handle** out) {
   h->device = device;
   h->fp64 = (p->precision == FCM_FP64);
   h->pairs_on = pairs_on;
+  h->max_systems = max_systems;
+  const int gsys = h->fp64 ? 1 : max_systems;   // the FP64 path runs a batch one system at a time
   DeviceGuard guard(device);
   int tile[3];
   if (h->fp64) { tile[0] = tile[1] = tile[2] = std::min(8, std::min(p->M[0], std::min(p->M[1], p->M[2]))); }
   else choose_tile(*p, tile);
   for (int d = 0; d < 3; ++d) h->p.tile[d] = tile[d];
-  fill_geometry(h->p, tile, &h->gf);
-  fill_geometry(h->p, tile, &h->gd);
+  fill_geometry(h->p, tile, &h->gf, max_systems);
+  fill_geometry(h->p, tile, &h->gd, max_systems);
   fill_kernel_consts(h->p, SigmaD, &h->kf);
   fill_kernel_consts(h->p, SigmaD, &h->kd);
   make_pair_consts(p->a, p->eta, p->Sigma, SigmaD, pairs_on ? p->r_c : 0.0, 0.5 * sg, &h->pd);
@@ -558,12 +699,17 @@ int fcm_create(const fcm_params* p, int device, fcm_handle** out) {
   const size_t mtot = (size_t)p->M[0] * p->M[1] * p->M[2];
   const size_t ncplx = (size_t)(p->M[0] / 2 + 1) * p->M[1] * p->M[2];
   BinBuffers& b = h->bb;
-  b.ntiles = h->gf.ntile[0] * h->gf.ntile[1] * h->gf.ntile[2];
-  const double ncells_d = (double)h->gf.mcell[0] * h->gf.mcell[1] * h->gf.mcell[2];
+  const double ntiles_d = (double)h->gf.ntile[0] * h->gf.ntile[1] * h->gf.ntile[2] * gsys;
+  const double ncells_d = (double)h->gf.mcell[0] * h->gf.mcell[1] * h->gf.mcell[2] * gsys;
   if (pairs_on && ncells_d > (double)(1u << 26)) {
     release(h);
     return fail(FCM_ERR_ARG, "too many pair cells (r_c too small for L)");
   }
+  if (ntiles_d > (double)(1u << 28)) {
+    release(h);
+    return fail(FCM_ERR_ARG, "too many tiles for one pass (grid or max_systems too large)");
+  }
+  b.ntiles = (int)ntiles_d;
   b.ncells = pairs_on ? (int)ncells_d : 1;
   A((void**)&b.tile_key, 4 * n); A((void**)&b.tile_rank, 4 * n);
   A((void**)&b.cell_key, 4 * n); A((void**)&b.cell_rank, 4 * n);
@@ -572,10 +718,12 @@ int fcm_create(const fcm_params* p, int device, fcm_handle** out) {
   A(&b.t_pos, v4 * n); A(&b.t_F, v4 * n); A(&b.t_T, v4 * n);
   A(&b.c_pos, v4 * n); A(&b.c_F, v4 * n); A(&b.c_T, v4 * n);
   A((void**)&b.status, 256);
+  A((void**)&h->sys_off, sizeof(int) * (kMaxBatch + 1));
   A(&h->upair, 3 * rsz * n); A(&h->wpair, 3 * rsz * n); A(&h->wscratch, 3 * rsz * n);
   h->grid_bytes = 3 * rsz * mtot;
-  A(&h->grid, h->grid_bytes);
-  A(&h->spec, 3 * 2 * rsz * ncplx);
+  h->spec_bytes = 3 * 2 * rsz * ncplx;
+  A(&h->grid, h->grid_bytes * gsys);
+  A(&h->spec, h->spec_bytes * gsys);
   void* table = nullptr;
   if (!h->fp64 && pairs_on) A(&table, sizeof(float4) * 5 * kPairTableIntervals);
   if (rc != FCM_OK) { std::string e = g_error; release(h); return fail(rc, e); }
@@ -600,19 +748,51 @@ int fcm_create(const fcm_params* p, int device, fcm_handle** out) {
   if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
   if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
   if (ce != cudaSuccess) { release(h); return fail(FCM_ERR_CUDA, std::string("setup: ") + cudaGetErrorString(ce)); }
+  // One R2C and one C2R plan per bucket of systems (3 transforms per system), all with one work
+  // area of the largest size any of them needs.
   int dims[3] = {p->M[2], p->M[1], p->M[0]};
-  cufftResult fr = cufftPlanMany(&h->r2c, 3, dims, nullptr, 1, (int)mtot, nullptr, 1, (int)ncplx,
-                                 h->fp64 ? CUFFT_D2Z : CUFFT_R2C, 3);
-  if (fr == CUFFT_SUCCESS) {
-    fr = cufftPlanMany(&h->c2r, 3, dims, nullptr, 1, (int)ncplx, nullptr, 1, (int)mtot,
-                       h->fp64 ? CUFFT_Z2D : CUFFT_C2R, 3);
-    if (fr != CUFFT_SUCCESS) cufftDestroy(h->r2c);
+  std::vector<int> buckets;
+  for (int k = 1; k < gsys; k *= 2) buckets.push_back(k);
+  buckets.push_back(gsys);
+  size_t work = 0;
+  for (int nb : buckets) {
+    fcm_handle::Plan pl{nb, 0, 0};
+    size_t w1 = 0, w2 = 0;
+    cufftResult fr = cufftCreate(&pl.r2c);
+    if (fr == CUFFT_SUCCESS) {
+      fr = cufftCreate(&pl.c2r);
+      if (fr != CUFFT_SUCCESS) cufftDestroy(pl.r2c);
+    }
+    if (fr == CUFFT_SUCCESS) {
+      h->plans.push_back(pl);
+      fr = cufftSetAutoAllocation(pl.r2c, 0);
+      if (fr == CUFFT_SUCCESS) fr = cufftSetAutoAllocation(pl.c2r, 0);
+      if (fr == CUFFT_SUCCESS)
+        fr = cufftMakePlanMany(pl.r2c, 3, dims, nullptr, 1, (int)mtot, nullptr, 1, (int)ncplx,
+                               h->fp64 ? CUFFT_D2Z : CUFFT_R2C, 3 * nb, &w1);
+      if (fr == CUFFT_SUCCESS)
+        fr = cufftMakePlanMany(pl.c2r, 3, dims, nullptr, 1, (int)ncplx, nullptr, 1, (int)mtot,
+                               h->fp64 ? CUFFT_Z2D : CUFFT_C2R, 3 * nb, &w2);
+    }
+    if (fr != CUFFT_SUCCESS) {
+      release(h);
+      return fail(FCM_ERR_CUFFT, "cuFFT plan for " + std::to_string(nb) + " systems failed: " + std::to_string((int)fr));
+    }
+    work = std::max(work, std::max(w1, w2));
   }
-  if (fr != CUFFT_SUCCESS) { release(h); return fail(FCM_ERR_CUFFT, "cufftPlanMany failed: " + std::to_string((int)fr)); }
-  h->plans = true;
-  size_t ws = 0;
-  if (cufftGetSize(h->r2c, &ws) == CUFFT_SUCCESS) h->bytes += ws;
-  if (cufftGetSize(h->c2r, &ws) == CUFFT_SUCCESS) h->bytes += ws;
+  A(&h->fft_work, work);
+  if (rc != FCM_OK) { std::string e = g_error; release(h); return fail(rc, e); }
+  for (auto& pl : h->plans) {
+    if (cufftSetWorkArea(pl.r2c, h->fft_work) != CUFFT_SUCCESS || cufftSetWorkArea(pl.c2r, h->fft_work) != CUFFT_SUCCESS) {
+      release(h);
+      return fail(FCM_ERR_CUFFT, "cufftSetWorkArea failed");
+    }
+  }
+  // extra grids of a bucket start at zero and stay zero (every pass zeroes the bucket's grids)
+  if (cudaMemset(h->grid, 0, h->grid_bytes * gsys) != cudaSuccess) {
+    release(h);
+    return fail(FCM_ERR_CUDA, "grid initialisation failed");
+  }
   if (cudaDeviceSynchronize() != cudaSuccess) { release(h); return fail(FCM_ERR_CUDA, "setup synchronisation failed"); }
   *out = h;
   return FCM_OK;
@@ -631,6 +811,18 @@ int fcm_apply_stages(fcm_handle* h, int n, const void* pos, const void* F, const
                      int stages, void* stream) {
   return apply_common(h, n, pos, F, T, U, W, stages, false, stream);
 }
+
+int fcm_batch_apply(fcm_handle* h, int n_sys, const int* offsets, const void* pos, const void* F, const void* T,
+                    void* U, void* W, void* stream) {
+  return batch_common(h, n_sys, offsets, pos, F, T, U, W, FCM_STAGE_ALL, stream);
+}
+
+int fcm_batch_apply_stages(fcm_handle* h, int n_sys, const int* offsets, const void* pos, const void* F,
+                           const void* T, void* U, void* W, int stages, void* stream) {
+  return batch_common(h, n_sys, offsets, pos, F, T, U, W, stages, stream);
+}
+
+int fcm_max_systems(const fcm_handle* h) { return h ? h->max_systems : 0; }
 
 int fcm_spread(fcm_handle* h, int n, const void* pos, const void* F, const void* T, void* stream) {
   return apply_common(h, n, pos, F, T, nullptr, nullptr, FCM_STAGE_GRID, true, stream);

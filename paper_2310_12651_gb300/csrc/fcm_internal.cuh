@@ -58,6 +58,13 @@ struct Geometry {
   int mcell[3];  // pair cells per dimension, max(int(L_i / r_c), 3)
   int shift;     // 1 if every mcell >= 4: the 27-cell neighbourhood never meets itself, so a
                  // neighbour cell's periodic image relative to the centre cell is unique
+  // Batched launches: nsys systems with these parameters, stacked. Tile t of the launch belongs
+  // to system t / tiles_per, pair cell c to system c / cells_per, and system s's grid starts
+  // grid_stride reals after system s-1's. nsys <= 1 is one system (the other fields unused).
+  int nsys;
+  int tiles_per;       // ntile[0] ntile[1] ntile[2]
+  int cells_per;       // mcell[0] mcell[1] mcell[2]
+  long long grid_stride;  // 3 M_x M_y M_z
 };
 
 // Position wrapped into [0, L): y - L floor(y / L), with the product rounded on
@@ -242,7 +249,16 @@ struct BinBuffers {
   void* t_pos; void* t_F; void* t_T;   // tile-sorted Vec4<R>
   void* c_pos; void* c_F; void* c_T;   // cell-sorted Vec4<R>
   int* status;
+  // Batched launches: particles of system s are rows sys_off[s] .. sys_off[s+1]-1 of the stacked
+  // inputs (device array of nsys + 1 ints); nsys <= 1 or sys_off == nullptr is one system.
+  const int* sys_off; int nsys;
 };
+
+// Largest number of systems in one batched pass.
+constexpr int kMaxBatch = 1024;
+struct SysOffsets { int off[kMaxBatch + 1]; };
+// Writes the first n + 1 offsets into device memory (a kernel, so graph capture can record it).
+void launch_write_offsets(const SysOffsets& o, int n, int* dst, cudaStream_t s, long long* launches);
 
 template <typename R>
 void launch_binning(const Geometry<R>& g, int n, const R* pos, const R* F, const R* T,
@@ -281,5 +297,10 @@ int record_error(int code, const char* msg);
 
 // Zero-fill of a device range (a kernel of this library, counted as a launch).
 void launch_zero(void* p, size_t bytes, cudaStream_t s, long long* launches);
+
+// U[k] += up[k] for k < count, and W[k] += wp[k] when W is non-null (the join of the grid part
+// and the pair sums, both in input order).
+template <typename R>
+void launch_add(R* U, const R* up, R* W, const R* wp, size_t count, cudaStream_t s, long long* launches);
 
 }  // namespace fcm

@@ -28,7 +28,9 @@ __global__ void __launch_bounds__(256) gather_tile_kernel(Geometry<float> g, Ker
   const int t = blockIdx.x;
   const int p0 = tstart[t], p1 = tstart[t + 1];
   if (p0 >= p1) return;
-  const TileOrigin o = tile_origin(g, t);
+  size_t goff;
+  const TileOrigin o = tile_origin(g, local_tile(g, t, &goff));
+  grid += goff;
   const int MG = GUARD ? g.MG : MGT;
   const ExtLayout l = ext_layout(g.tile, MG);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;

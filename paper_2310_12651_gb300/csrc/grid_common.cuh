@@ -53,6 +53,18 @@ __device__ inline TileOrigin tile_origin(const Geometry<float>& g, int t) {
   return o;
 }
 
+// Tile t of a (possibly batched) launch: the tile's index inside its system, and in *grid_off
+// the offset (reals) of that system's grid.
+__device__ inline int local_tile(const Geometry<float>& g, int t, size_t* grid_off) {
+  if (g.nsys > 1) {
+    const int s = t / g.tiles_per;
+    *grid_off = (size_t)s * (size_t)g.grid_stride;
+    return t - s * g.tiles_per;
+  }
+  *grid_off = 0;
+  return t;
+}
+
 __device__ inline int wrap_index(int i, int M) {
   while (i >= M) i -= M;
   return i;

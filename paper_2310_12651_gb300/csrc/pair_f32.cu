@@ -79,6 +79,7 @@ __device__ inline void eval_pair(const PairConsts<float>& pc, const PairTable& t
 
 constexpr int kCellWarps = 8;
 constexpr int kCandChunk = 1536;
+static_assert(kCandChunk % 64 == 0, "candidate chunks are padded to whole 64-candidate passes");
 constexpr int kIBatch = 256;
 constexpr int kMaxPieces = 18;
 
@@ -120,7 +121,10 @@ __global__ void __launch_bounds__(kCellWarps * 32, 2) pair_cell_kernel(Geometry<
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int mx = g.mcell[0], my = g.mcell[1], mz = g.mcell[2];
   if (threadIdx.x == 0) {
-    const int cx = cell % mx, cy = (cell / mx) % my, cz = cell / (mx * my);
+    const int cs = g.nsys > 1 ? cell / g.cells_per : 0;   // system of this cell (batched launches)
+    const int cbase = cs * g.cells_per;
+    const int lc = cell - cbase;
+    const int cx = lc % mx, cy = (lc / mx) % my, cz = lc / (mx * my);
     int np = 0, total = 0;
     for (int ddz = -1; ddz <= 1; ++ddz) {
       const int zu = cz + ddz;
@@ -129,7 +133,7 @@ __global__ void __launch_bounds__(kCellWarps * 32, 2) pair_cell_kernel(Geometry<
       for (int ddy = -1; ddy <= 1; ++ddy) {
         const int yu = cy + ddy;
         const float sy = yu < 0 ? -g.L[1] : (yu >= my ? g.L[1] : 0.f);
-        const int rowbase = mx * (pmod(yu, my) + my * zc);
+        const int rowbase = cbase + mx * (pmod(yu, my) + my * zc);
         int ra[2], rb[2], k = 0;
         float sx[2] = {0.f, 0.f};
         if (cx - 1 >= 0 && cx + 1 < mx) { ra[0] = cx - 1; rb[0] = cx + 1; k = 1; }
@@ -173,6 +177,10 @@ __global__ void __launch_bounds__(kCellWarps * 32, 2) pair_cell_kernel(Geometry<
           if (TORQUE) sT[lo - cb + k] = cT[src + k];
         }
       }
+      // pad to whole 64-candidate passes with far-away dummies (index -1): no bounds test in the loop
+      const int ncp = (nc + 63) & ~63;
+      for (int k = nc + threadIdx.x; k < ncp; k += blockDim.x)
+        spos[k] = make_float4(1e18f, 1e18f, 1e18f, __int_as_float(-1));
       __syncthreads();
       for (int il = warp; il < ni; il += kCellWarps) {
         const float4 yi = cpos[ib + il];
@@ -180,35 +188,38 @@ __global__ void __launch_bounds__(kCellWarps * 32, 2) pair_cell_kernel(Geometry<
         Neu u[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         Neu w[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         int qh = 0, qn = 0;
-        for (int base = 0; base < nc; base += 32) {
-          const int j = base + lane;
-          bool hit = false;
-          float4 dq = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (j < nc) {
-            const float4 yj = spos[j];
-            if (__float_as_int(yj.w) != self) {
-              dq.x = SHIFT ? yi.x - yj.x : min_image(yi.x - yj.x, g.L[0]);
-              dq.y = SHIFT ? yi.y - yj.y : min_image(yi.y - yj.y, g.L[1]);
-              dq.z = SHIFT ? yi.z - yj.z : min_image(yi.z - yj.z, g.L[2]);
-              dq.w = dq.x * dq.x + dq.y * dq.y + dq.z * dq.z;
-              hit = dq.w < pc.rc2;
+        for (int base = 0; base < ncp; base += 64) {
+          // two warp passes per iteration: both candidates' tests are issued before either push
+          float4 dq[2];
+          bool hit[2];
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            const float4 yj = spos[base + 32 * k + lane];
+            dq[k].x = SHIFT ? yi.x - yj.x : min_image(yi.x - yj.x, g.L[0]);
+            dq[k].y = SHIFT ? yi.y - yj.y : min_image(yi.y - yj.y, g.L[1]);
+            dq[k].z = SHIFT ? yi.z - yj.z : min_image(yi.z - yj.z, g.L[2]);
+            dq[k].w = dq[k].x * dq[k].x + dq[k].y * dq[k].y + dq[k].z * dq[k].z;
+            hit[k] = dq[k].w < pc.rc2 && __float_as_int(yj.w) != self;
+          }
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            const unsigned m = __ballot_sync(kFullMask, hit[k]);
+            if (hit[k]) {
+              const int slot = (qh + qn + __popc(m & lt)) & (kQueue - 1);
+              myqd[slot] = dq[k];
+              myqj[slot] = base + 32 * k + lane;
             }
-          }
-          const unsigned m = __ballot_sync(kFullMask, hit);
-          if (hit) {
-            const int slot = (qh + qn + __popc(m & lt)) & (kQueue - 1);
-            myqd[slot] = dq;
-            myqj[slot] = j;
-          }
-          qn += __popc(m);
-          __syncwarp();
-          if (qn >= 32) {
-            const int slot = (qh + lane) & (kQueue - 1);
-            const int jj = myqj[slot];
-            eval_pair<TORQUE>(pc, tab, myqd[slot], sF[jj], TORQUE ? sT[jj] : make_float4(0.f, 0.f, 0.f, 0.f), u, w);
-            qh = (qh + 32) & (kQueue - 1);
-            qn -= 32;
+            qn += __popc(m);
             __syncwarp();
+            if (qn >= 32) {
+              const int slot = (qh + lane) & (kQueue - 1);
+              const int jj = myqj[slot];
+              eval_pair<TORQUE>(pc, tab, myqd[slot], sF[jj], TORQUE ? sT[jj] : make_float4(0.f, 0.f, 0.f, 0.f), u,
+                                w);
+              qh = (qh + 32) & (kQueue - 1);
+              qn -= 32;
+              __syncwarp();
+            }
           }
         }
         if (lane < qn) {

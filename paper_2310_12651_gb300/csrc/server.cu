@@ -1,0 +1,605 @@
+// Serving engine: many independent mobility products from many host threads on
+// one GPU.
+//
+// The paper computes one system per call. A service sees a stream of requests
+// of every size and box; launching each alone leaves the GPU idle between small
+// launches and re-plans FFTs for every box. Here:
+//
+//   * requests with identical parameters (a "grid class": box, grid, kernel
+//     widths, cutoff, precision, torques or not) waiting at the same time are
+//     stacked into one fcm_batch_apply pass (continuous batching: whatever is
+//     queued when a launch slot frees up goes into the next pass);
+//   * batch handles (workspace, cell lists, cuFFT plans) stay resident in a
+//     cache keyed by grid class and capacity bucket, so a class's second pass
+//     plans and allocates nothing;
+//   * the cache is bounded by an HBM budget: before a new handle is created,
+//     idle handles are evicted least recently used first; a request whose
+//     handle alone exceeds the budget is rejected (FCM_ERR_OOM);
+//   * two launch slots, each with its own stream and pinned staging, so one
+//     pass's copies and kernels overlap the next pass's (also across classes);
+//   * every wait is bounded (poll timeouts; the worker polls events).
+//
+// One worker thread owns every CUDA object; submit/poll/cancel/stats only take
+// the request table's lock.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <list>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/fcm.h"
+#include "fcm_internal.cuh"
+
+namespace fcm {
+int check_params(const fcm_params* p, std::string* why);
+size_t workspace_estimate(const fcm_params& p, int max_systems);
+}  // namespace fcm
+
+using namespace fcm;
+using Clock = std::chrono::steady_clock;
+
+namespace {
+
+int fail(int code, const std::string& msg) { return record_error(code, msg.c_str()); }
+
+size_t pow2_at_least(size_t v, size_t lo) {
+  size_t p = lo;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+enum State { kPending = 0, kRunning = 1, kDone = 2 };
+
+struct Request {
+  long long id = 0;
+  fcm_request r{};
+  std::string key;
+  bool torque = false;
+  size_t rsz = 4;
+  int state = kPending;
+  int status = FCM_OK;
+  Clock::time_point t_submit, t_done;
+};
+
+struct CachedHandle {
+  std::string key;
+  fcm_handle* h = nullptr;
+  int max_systems = 0;
+  int max_n = 0;
+  size_t bytes = 0;
+  cudaEvent_t last = nullptr;   // last pass enqueued on this handle
+  int in_flight = 0;            // slots whose pass uses it
+  unsigned long long last_use = 0;
+};
+
+struct Buffer {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct Slot {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  Buffer h_in, h_out, d_in, d_out;   // pinned host and device staging
+  std::vector<std::shared_ptr<Request>> reqs;
+  std::vector<int> offsets;
+  CachedHandle* ch = nullptr;
+  bool busy = false;
+  bool torque = false;
+  size_t rsz = 4;
+  int n = 0;
+};
+
+constexpr int kSlots = 2;
+constexpr size_t kLatencyWindow = 1 << 17;
+
+}  // namespace
+
+struct fcm_server {
+  int device = 0;
+  size_t budget = 0;
+  int max_batch = 1;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  bool stop = false;
+  long long next_id = 1;
+  std::deque<std::shared_ptr<Request>> pending;
+  std::unordered_map<long long, std::shared_ptr<Request>> table;
+  // stats (under mu)
+  long long submitted = 0, completed = 0, rejected = 0, canceled = 0, failed = 0;
+  long long batches = 0, batched_requests = 0, handles_created = 0, handles_evicted = 0;
+  std::vector<double> latency_us;   // ring of the latest completions
+  size_t latency_next = 0;
+  size_t hbm_bytes = 0;             // written by the worker, read under mu
+  // worker-owned
+  std::list<CachedHandle> cache;
+  Slot slots[kSlots];
+  size_t used = 0;                  // handles + staging device bytes
+  unsigned long long tick = 0;
+  std::thread worker;
+  int init_status = FCM_OK;
+  std::string init_error;
+};
+
+namespace {
+
+// The grid class of a request: every parameter that shapes the pass, field by field (the
+// struct's padding bytes are not part of it).
+std::string class_key(const fcm_params& p, bool torque) {
+  const double d[9] = {p.L[0], p.L[1], p.L[2], p.a, p.eta, p.Sigma, p.Sigma_D == 0.0 ? p.Sigma : p.Sigma_D, p.r_c,
+                       torque ? 1.0 : 0.0};
+  const int i[5] = {p.M[0], p.M[1], p.M[2], p.M_G, p.precision};
+  std::string k(reinterpret_cast<const char*>(d), sizeof(d));
+  k.append(reinterpret_cast<const char*>(i), sizeof(i));
+  return k;
+}
+
+void record_latency(fcm_server* s, double us) {
+  if (s->latency_us.size() < kLatencyWindow) s->latency_us.push_back(us);
+  else s->latency_us[s->latency_next] = us;
+  s->latency_next = (s->latency_next + 1) % kLatencyWindow;
+}
+
+// Completes requests (state, status, latency) and wakes pollers. Caller holds no lock.
+void finish_requests(fcm_server* s, std::vector<std::shared_ptr<Request>>& reqs, int status) {
+  std::lock_guard<std::mutex> lock(s->mu);
+  const Clock::time_point now = Clock::now();
+  for (auto& r : reqs) {
+    r->state = kDone;
+    r->status = status;
+    r->t_done = now;
+    if (status == FCM_OK) {
+      ++s->completed;
+      record_latency(s, std::chrono::duration<double, std::micro>(now - r->t_submit).count());
+    } else if (status == FCM_ERR_OOM) {
+      ++s->rejected;
+    } else {
+      ++s->failed;
+    }
+  }
+  s->hbm_bytes = s->used;
+  s->cv_done.notify_all();
+}
+
+int grow(Buffer* b, size_t bytes, bool host, size_t* used) {
+  if (b->bytes >= bytes) return FCM_OK;
+  const size_t want = pow2_at_least(bytes, 1 << 16);
+  if (b->p) {
+    if (host) cudaFreeHost(b->p);
+    else { cudaFree(b->p); *used -= b->bytes; }
+    b->p = nullptr;
+    b->bytes = 0;
+  }
+  cudaError_t e = host ? cudaMallocHost(&b->p, want) : cudaMalloc(&b->p, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    b->p = nullptr;
+    return fail(FCM_ERR_OOM, std::string("staging allocation failed: ") + cudaGetErrorString(e));
+  }
+  b->bytes = want;
+  if (!host) *used += want;
+  return FCM_OK;
+}
+
+void destroy_handle(fcm_server* s, std::list<CachedHandle>::iterator it) {
+  if (it->last) cudaEventDestroy(it->last);
+  fcm_destroy(it->h);
+  s->used -= it->bytes;
+  s->cache.erase(it);
+}
+
+// Completes a slot whose pass has finished: results to the callers' buffers.
+void complete_slot(fcm_server* s, Slot& sl, int status) {
+  if (status == FCM_OK) {
+    const size_t row = 3 * sl.rsz;
+    const size_t ntot = (size_t)sl.n;
+    const char* U = static_cast<const char*>(sl.h_out.p);
+    const char* W = U + ntot * row;
+    for (size_t k = 0; k < sl.reqs.size(); ++k) {
+      Request& r = *sl.reqs[k];
+      const size_t o = (size_t)sl.offsets[k] * row, bytes = (size_t)r.r.n * row;
+      if (bytes == 0) continue;
+      std::memcpy(r.r.U, U + o, bytes);
+      if (r.r.W) std::memcpy(r.r.W, W + o, bytes);
+    }
+  }
+  if (sl.ch) sl.ch->in_flight -= 1;
+  sl.ch = nullptr;
+  sl.busy = false;
+  finish_requests(s, sl.reqs, status);
+  sl.reqs.clear();
+}
+
+// Polls the slots; completes finished passes. Returns true if any finished.
+bool reap(fcm_server* s) {
+  bool any = false;
+  for (Slot& sl : s->slots) {
+    if (!sl.busy) continue;
+    cudaError_t q = cudaEventQuery(sl.done);
+    if (q == cudaErrorNotReady) continue;
+    if (q != cudaSuccess) {
+      record_error(FCM_ERR_CUDA, cudaGetErrorString(q));
+      complete_slot(s, sl, FCM_ERR_CUDA);
+    } else {
+      complete_slot(s, sl, FCM_OK);
+    }
+    any = true;
+  }
+  return any;
+}
+
+bool any_busy(const fcm_server* s) {
+  for (const Slot& sl : s->slots)
+    if (sl.busy) return true;
+  return false;
+}
+
+// A cached handle for the class with room for (systems, n), creating one within the budget.
+int get_handle(fcm_server* s, const fcm_params& p, const std::string& key, int systems, int n, CachedHandle** out) {
+  *out = nullptr;
+  for (auto it = s->cache.begin(); it != s->cache.end(); ++it) {
+    if (it->key == key && it->max_systems >= systems && it->max_n >= n) {
+      it->last_use = ++s->tick;
+      *out = &*it;
+      return FCM_OK;
+    }
+  }
+  fcm_params q = p;
+  const int want_sys = (int)std::min<size_t>(pow2_at_least(systems, 1), s->max_batch);
+  q.max_n = (int)std::min<size_t>(pow2_at_least((size_t)n, 1024), (size_t)1 << 30);
+  q.tile[0] = q.tile[1] = q.tile[2] = 0;
+  q.spread_kernel = 0;
+  const size_t est = workspace_estimate(q, want_sys);
+  if (est > s->budget)
+    return fail(FCM_ERR_OOM, "the request's workspace (" + std::to_string(est) + " bytes) exceeds the HBM budget (" +
+                                 std::to_string(s->budget) + " bytes)");
+  // evict idle handles, least recently used first; wait for passes in flight if that is not enough
+  for (;;) {
+    if (s->used + est <= s->budget) break;
+    auto victim = s->cache.end();
+    for (auto it = s->cache.begin(); it != s->cache.end(); ++it)
+      if (it->in_flight == 0 && (victim == s->cache.end() || it->last_use < victim->last_use)) victim = it;
+    if (victim != s->cache.end()) {
+      destroy_handle(s, victim);
+      std::lock_guard<std::mutex> lock(s->mu);
+      ++s->handles_evicted;
+      continue;
+    }
+    if (!any_busy(s)) break;   // only staging remains; try anyway
+    if (!reap(s)) std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  fcm_handle* h = nullptr;
+  int rc = fcm_create_batch(&q, want_sys, s->device, &h);
+  if (rc != FCM_OK) return rc;
+  CachedHandle ch;
+  ch.key = key;
+  ch.h = h;
+  ch.max_systems = want_sys;
+  ch.max_n = q.max_n;
+  ch.bytes = fcm_workspace_bytes(h);
+  ch.last_use = ++s->tick;
+  if (cudaEventCreateWithFlags(&ch.last, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    fcm_destroy(h);
+    return fail(FCM_ERR_CUDA, "event creation failed");
+  }
+  s->used += ch.bytes;
+  s->cache.push_back(ch);
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    ++s->handles_created;
+  }
+  *out = &s->cache.back();
+  return FCM_OK;
+}
+
+// Takes the oldest pending request and every pending request of its class (FIFO), up to the
+// batch limits. Called with s->mu held.
+std::vector<std::shared_ptr<Request>> take_batch(fcm_server* s) {
+  std::vector<std::shared_ptr<Request>> b;
+  if (s->pending.empty()) return b;
+  const std::string key = s->pending.front()->key;
+  long long total = 0;
+  for (auto it = s->pending.begin(); it != s->pending.end() && (int)b.size() < s->max_batch;) {
+    if ((*it)->key == key && (b.empty() || total + (*it)->r.n <= (1LL << 28))) {
+      total += (*it)->r.n;
+      (*it)->state = kRunning;
+      b.push_back(*it);
+      it = s->pending.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  return b;
+}
+
+// Stages a batch into a slot and enqueues its pass.
+int launch(fcm_server* s, Slot& sl, std::vector<std::shared_ptr<Request>>& reqs) {
+  const Request& r0 = *reqs.front();
+  sl.rsz = r0.rsz;
+  sl.torque = r0.torque;
+  sl.offsets.assign(reqs.size() + 1, 0);
+  for (size_t k = 0; k < reqs.size(); ++k) sl.offsets[k + 1] = sl.offsets[k] + reqs[k]->r.n;
+  sl.n = sl.offsets.back();
+  const size_t row = 3 * sl.rsz, ntot = (size_t)sl.n;
+  const size_t in_bytes = (sl.torque ? 3 : 2) * ntot * row, out_bytes = 2 * ntot * row;
+  CachedHandle* ch = nullptr;
+  int rc = get_handle(s, r0.r.params, r0.key, (int)reqs.size(), sl.n, &ch);
+  if (rc != FCM_OK) return rc;
+  if ((rc = grow(&sl.h_in, in_bytes, true, &s->used)) || (rc = grow(&sl.h_out, out_bytes, true, &s->used)) ||
+      (rc = grow(&sl.d_in, in_bytes, false, &s->used)) || (rc = grow(&sl.d_out, out_bytes, false, &s->used)))
+    return rc;
+  char* hin = static_cast<char*>(sl.h_in.p);
+  for (size_t k = 0; k < reqs.size(); ++k) {
+    const fcm_request& q = reqs[k]->r;
+    const size_t o = (size_t)sl.offsets[k] * row, bytes = (size_t)q.n * row;
+    if (bytes == 0) continue;
+    std::memcpy(hin + o, q.pos, bytes);
+    std::memcpy(hin + ntot * row + o, q.F, bytes);
+    if (sl.torque) {
+      if (q.T) std::memcpy(hin + 2 * ntot * row + o, q.T, bytes);
+      else std::memset(hin + 2 * ntot * row + o, 0, bytes);
+    }
+  }
+  char* din = static_cast<char*>(sl.d_in.p);
+  char* dout = static_cast<char*>(sl.d_out.p);
+  auto cuda = [&](cudaError_t e, const char* what) -> int {
+    if (e == cudaSuccess) return FCM_OK;
+    cudaGetLastError();
+    return fail(FCM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  };
+  if ((rc = cuda(cudaMemcpyAsync(din, hin, in_bytes, cudaMemcpyHostToDevice, sl.stream), "input copy"))) return rc;
+  if ((rc = cuda(cudaStreamWaitEvent(sl.stream, ch->last, 0), "handle ordering"))) return rc;
+  const int nsys = (int)reqs.size();
+  if (ch->max_systems >= nsys) {
+    rc = fcm_batch_apply(ch->h, nsys, sl.offsets.data(), din, din + ntot * row, sl.torque ? din + 2 * ntot * row : nullptr,
+                         dout, sl.torque ? dout + ntot * row : nullptr, sl.stream);
+  } else {
+    rc = fail(FCM_ERR_ARG, "batch larger than the handle");
+  }
+  if (rc != FCM_OK) return rc;
+  if ((rc = cuda(cudaEventRecord(ch->last, sl.stream), "event"))) return rc;
+  if ((rc = cuda(cudaMemcpyAsync(sl.h_out.p, dout, out_bytes, cudaMemcpyDeviceToHost, sl.stream), "output copy")))
+    return rc;
+  if ((rc = cuda(cudaEventRecord(sl.done, sl.stream), "event"))) return rc;
+  ch->in_flight += 1;
+  ch->last_use = ++s->tick;
+  sl.ch = ch;
+  sl.reqs = reqs;
+  sl.busy = true;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    ++s->batches;
+    s->batched_requests += (long long)reqs.size();
+    s->hbm_bytes = s->used;
+  }
+  return FCM_OK;
+}
+
+void worker_main(fcm_server* s) {
+  cudaSetDevice(s->device);
+  for (;;) {
+    bool progressed = reap(s);
+    Slot* free_slot = nullptr;
+    for (Slot& sl : s->slots)
+      if (!sl.busy) { free_slot = &sl; break; }
+    std::vector<std::shared_ptr<Request>> batch;
+    {
+      std::unique_lock<std::mutex> lock(s->mu);
+      if (s->stop) break;
+      if (free_slot) batch = take_batch(s);
+      if (batch.empty() && !progressed) {
+        if (any_busy(s)) {
+          lock.unlock();
+          std::this_thread::sleep_for(std::chrono::microseconds(20));
+        } else {
+          s->cv_work.wait_for(lock, std::chrono::milliseconds(5), [&] { return s->stop || !s->pending.empty(); });
+        }
+        continue;
+      }
+    }
+    if (!batch.empty()) {
+      int rc = launch(s, *free_slot, batch);
+      if (rc != FCM_OK) finish_requests(s, batch, rc);
+    }
+  }
+  // shutdown: let passes in flight end (kernels are finite), then release everything
+  for (Slot& sl : s->slots) {
+    if (sl.busy) {
+      cudaError_t e = cudaEventSynchronize(sl.done);
+      complete_slot(s, sl, e == cudaSuccess ? FCM_OK : FCM_ERR_CUDA);
+    }
+  }
+}
+
+void release_server(fcm_server* s) {
+  cudaSetDevice(s->device);
+  while (!s->cache.empty()) destroy_handle(s, s->cache.begin());
+  for (Slot& sl : s->slots) {
+    if (sl.h_in.p) cudaFreeHost(sl.h_in.p);
+    if (sl.h_out.p) cudaFreeHost(sl.h_out.p);
+    if (sl.d_in.p) cudaFree(sl.d_in.p);
+    if (sl.d_out.p) cudaFree(sl.d_out.p);
+    if (sl.done) cudaEventDestroy(sl.done);
+    if (sl.stream) cudaStreamDestroy(sl.stream);
+  }
+  delete s;
+}
+
+}  // namespace
+
+#pragma GCC visibility push(default)
+extern "C" {
+
+int fcm_server_create(int device, size_t hbm_budget, int max_batch, fcm_server** out) {
+  if (!out) return fail(FCM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (max_batch < 1 || max_batch > FCM_MAX_BATCH)
+    return fail(FCM_ERR_ARG, "max_batch must be in [1, " + std::to_string(FCM_MAX_BATCH) + "]");
+  if (hbm_budget == 0) return fail(FCM_ERR_ARG, "hbm_budget must be > 0");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return fail(FCM_ERR_CUDA, "CUDA device " + std::to_string(device) + " is not available");
+  }
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(device);
+  fcm_server* s = new fcm_server();
+  s->device = device;
+  s->budget = hbm_budget;
+  s->max_batch = max_batch;
+  s->latency_us.reserve(1024);
+  cudaError_t e = cudaSuccess;
+  for (Slot& sl : s->slots) {
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+  }
+  cudaSetDevice(prev);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    release_server(s);
+    return fail(FCM_ERR_CUDA, std::string("server setup: ") + cudaGetErrorString(e));
+  }
+  s->worker = std::thread(worker_main, s);
+  *out = s;
+  return FCM_OK;
+}
+
+int fcm_server_submit(fcm_server* s, const fcm_request* r, long long* id) {
+  if (!s || !r || !id) return fail(FCM_ERR_ARG, "server, request and id must be non-NULL");
+  *id = 0;
+  std::string why;
+  if (!check_params(&r->params, &why)) {
+    std::lock_guard<std::mutex> lock(s->mu);
+    ++s->rejected;
+    return fail(FCM_ERR_ARG, why);
+  }
+  if (r->n < 0 || (r->n > 0 && (!r->pos || !r->F || !r->U))) {
+    std::lock_guard<std::mutex> lock(s->mu);
+    ++s->rejected;
+    return fail(FCM_ERR_ARG, "n must be >= 0 and pos, F, U non-NULL when n > 0");
+  }
+  auto q = std::make_shared<Request>();
+  q->r = *r;
+  q->torque = (r->T != nullptr) || (r->W != nullptr);
+  q->key = class_key(r->params, q->torque);
+  q->rsz = r->params.precision == FCM_FP64 ? sizeof(double) : sizeof(float);
+  q->t_submit = Clock::now();
+  std::lock_guard<std::mutex> lock(s->mu);
+  q->id = s->next_id++;
+  ++s->submitted;
+  s->table.emplace(q->id, q);
+  if (r->n == 0) {   // nothing to compute
+    q->state = kDone;
+    q->status = FCM_OK;
+    q->t_done = q->t_submit;
+    ++s->completed;
+    record_latency(s, 0.0);
+  } else {
+    s->pending.push_back(q);
+    s->cv_work.notify_one();
+  }
+  *id = q->id;
+  return FCM_OK;
+}
+
+int fcm_server_poll(fcm_server* s, long long id, long long timeout_us, int* status) {
+  if (!s || !status) return fail(FCM_ERR_ARG, "server and status must be non-NULL");
+  std::unique_lock<std::mutex> lock(s->mu);
+  auto it = s->table.find(id);
+  if (it == s->table.end()) return fail(FCM_ERR_ARG, "unknown request id " + std::to_string(id));
+  std::shared_ptr<Request> q = it->second;
+  if (q->state != kDone && timeout_us > 0)
+    s->cv_done.wait_for(lock, std::chrono::microseconds(timeout_us), [&] { return q->state == kDone; });
+  if (q->state != kDone) return fail(FCM_ERR_TIMEOUT, "request " + std::to_string(id) + " not finished");
+  *status = q->status;
+  s->table.erase(id);
+  return FCM_OK;
+}
+
+int fcm_server_cancel(fcm_server* s, long long id) {
+  if (!s) return fail(FCM_ERR_ARG, "server is NULL");
+  std::lock_guard<std::mutex> lock(s->mu);
+  auto it = s->table.find(id);
+  if (it == s->table.end()) return fail(FCM_ERR_ARG, "unknown request id " + std::to_string(id));
+  std::shared_ptr<Request> q = it->second;
+  if (q->state != kPending) return fail(FCM_ERR_BUSY, "request " + std::to_string(id) + " already launched or done");
+  for (auto p = s->pending.begin(); p != s->pending.end(); ++p)
+    if ((*p)->id == id) { s->pending.erase(p); break; }
+  q->state = kDone;
+  q->status = FCM_ERR_CANCELED;
+  q->t_done = Clock::now();
+  ++s->canceled;
+  s->cv_done.notify_all();
+  return FCM_OK;
+}
+
+int fcm_server_get_stats(fcm_server* s, fcm_server_stats* out) {
+  if (!s || !out) return fail(FCM_ERR_ARG, "server and out must be non-NULL");
+  std::vector<double> lat;
+  std::lock_guard<std::mutex> lock(s->mu);
+  std::memset(out, 0, sizeof(*out));
+  out->submitted = s->submitted;
+  out->completed = s->completed;
+  out->rejected = s->rejected;
+  out->canceled = s->canceled;
+  out->failed = s->failed;
+  out->pending = (long long)s->pending.size();
+  out->batches = s->batches;
+  out->batched_requests = s->batched_requests;
+  out->handles_created = s->handles_created;
+  out->handles_evicted = s->handles_evicted;
+  out->hbm_bytes = s->hbm_bytes;
+  out->hbm_budget = s->budget;
+  lat = s->latency_us;
+  if (!lat.empty()) {
+    auto pct = [&](double f) {
+      size_t k = (size_t)std::min<double>((double)lat.size() - 1, f * (double)(lat.size() - 1) + 0.5);
+      std::nth_element(lat.begin(), lat.begin() + k, lat.end());
+      return lat[k];
+    };
+    out->latency_p50_us = pct(0.50);
+    out->latency_p99_us = pct(0.99);
+    out->latency_max_us = *std::max_element(lat.begin(), lat.end());
+  }
+  return FCM_OK;
+}
+
+int fcm_server_reset_latency(fcm_server* s) {
+  if (!s) return fail(FCM_ERR_ARG, "server is NULL");
+  std::lock_guard<std::mutex> lock(s->mu);
+  s->latency_us.clear();
+  s->latency_next = 0;
+  return FCM_OK;
+}
+
+int fcm_server_destroy(fcm_server* s) {
+  if (!s) return FCM_OK;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->stop = true;
+    for (auto& q : s->pending) {
+      q->state = kDone;
+      q->status = FCM_ERR_CANCELED;
+      ++s->canceled;
+    }
+    s->pending.clear();
+    s->cv_work.notify_all();
+    s->cv_done.notify_all();
+  }
+  if (s->worker.joinable()) s->worker.join();
+  release_server(s);
+  return FCM_OK;
+}
+
+}  // extern "C"
+#pragma GCC visibility pop

@@ -1,9 +1,10 @@
 // Inverse Stokes operator in Fourier space (Section 2.1, step 2 (b)):
 //   u_k = (I - k k^T / k^2) f_k / (eta k^2),
 // applied in place to the three R2C spectra (layout [c][z][y][x], x halved to
-// M_x/2 + 1). The factor 1/M of the unnormalised inverse FFT is folded in. The
-// k = 0 mode and every mode with an index on a Nyquist plane (M_i/2 of an even
-// M_i) are set to zero. One thread per complex mode, 3 x 2 loads and stores.
+// M_x/2 + 1) of each system of a launch (blockIdx.y). The factor 1/M of the
+// unnormalised inverse FFT is folded in. The k = 0 mode and every mode with an
+// index on a Nyquist plane (M_i/2 of an even M_i) are set to zero. One thread
+// per complex mode, 3 x 2 loads and stores.
 #include <cuComplex.h>
 #include "fcm_internal.cuh"
 
@@ -25,6 +26,7 @@ __global__ void __launch_bounds__(256) project_kernel(Geometry<R> g, R scale, ty
   typedef typename Cplx<R>::T C2;
   size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (idx >= ncplx) return;
+  spec += (size_t)blockIdx.y * 3 * ncplx;   // system blockIdx.y of a batched launch
   const int Mh = g.M[0] / 2 + 1;
   int ix = (int)(idx % Mh);
   size_t rest = idx / Mh;
@@ -62,7 +64,8 @@ void launch_projection(const Geometry<R>& g, R eta, void* spectrum, cudaStream_t
   double mtot = (double)g.M[0] * g.M[1] * g.M[2];
   R scale = R(1.0 / ((double)eta * mtot));
   unsigned blocks = (unsigned)((ncplx + 255) / 256);
-  project_kernel<R><<<blocks, 256, 0, s>>>(g, scale, (typename Cplx<R>::T*)spectrum, ncplx);
+  const unsigned nsys = g.nsys > 1 ? (unsigned)g.nsys : 1u;
+  project_kernel<R><<<dim3(blocks, nsys), 256, 0, s>>>(g, scale, (typename Cplx<R>::T*)spectrum, ncplx);
   *launches += 1;
 }
 

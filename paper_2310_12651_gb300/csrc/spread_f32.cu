@@ -91,7 +91,9 @@ __global__ void __launch_bounds__(rows_threads(MGT), 1) spread_rows_kernel(Geome
   const int t = blockIdx.x;
   const int p0 = tstart[t], p1 = tstart[t + 1];
   if (p0 >= p1) return;
-  const TileOrigin o = tile_origin(g, t);
+  size_t goff;
+  const TileOrigin o = tile_origin(g, local_tile(g, t, &goff));
+  grid += goff;
   const int MG = GUARD ? g.MG : MGT;
   const int EY = g.tile[1] + MG - 1, EZ = g.tile[2] + MG - 1;
   const int R = EY * EZ;
@@ -194,7 +196,9 @@ __global__ void __launch_bounds__(256) spread_tile_kernel(Geometry<float> g, Ker
   const int t = blockIdx.x;
   const int p0 = tstart[t], p1 = tstart[t + 1];
   if (p0 >= p1) return;
-  const TileOrigin o = tile_origin(g, t);
+  size_t goff;
+  const TileOrigin o = tile_origin(g, local_tile(g, t, &goff));
+  grid += goff;
   const int MG = GUARD ? g.MG : MGT;
   const ExtLayout l = ext_layout(g.tile, MG);
   for (int k = threadIdx.x; k < 3 * l.C; k += blockDim.x) acc[k] = 0.f;

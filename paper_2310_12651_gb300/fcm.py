@@ -14,7 +14,8 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfcm.so")
 
-FCM_OK, FCM_ERR_ARG, FCM_ERR_OOM, FCM_ERR_CUDA, FCM_ERR_CUFFT, FCM_ERR_TIMEOUT, FCM_ERR_INPUT = range(7)
+(FCM_OK, FCM_ERR_ARG, FCM_ERR_OOM, FCM_ERR_CUDA, FCM_ERR_CUFFT, FCM_ERR_TIMEOUT, FCM_ERR_INPUT, FCM_ERR_BUSY,
+ FCM_ERR_CANCELED) = range(9)
 FCM_FP32, FCM_FP64 = 0, 1
 STAGE_GRID, STAGE_PAIR, STAGE_ALL = 1, 2, 3
 NUM_STAGES = 6
@@ -44,6 +45,30 @@ class Params(ctypes.Structure):
     ]
 
 
+class Request(ctypes.Structure):
+    _fields_ = [
+        ("params", Params),
+        ("n", ctypes.c_int),
+        ("pos", ctypes.c_void_p),
+        ("F", ctypes.c_void_p),
+        ("T", ctypes.c_void_p),
+        ("U", ctypes.c_void_p),
+        ("W", ctypes.c_void_p),
+    ]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_longlong) for name in
+                ("submitted", "completed", "rejected", "canceled", "failed", "pending", "batches", "batched_requests",
+                 "handles_created", "handles_evicted")] + [
+        ("hbm_bytes", ctypes.c_size_t),
+        ("hbm_budget", ctypes.c_size_t),
+        ("latency_p50_us", ctypes.c_double),
+        ("latency_p99_us", ctypes.c_double),
+        ("latency_max_us", ctypes.c_double),
+    ]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2310_12651_gb300.build.build()")
@@ -53,6 +78,10 @@ def _load():
         "fcm_version": (i, []),
         "fcm_params_default": (i, [ctypes.POINTER(Params)]),
         "fcm_create": (i, [ctypes.POINTER(Params), i, ctypes.POINTER(vp)]),
+        "fcm_create_batch": (i, [ctypes.POINTER(Params), i, i, ctypes.POINTER(vp)]),
+        "fcm_batch_apply": (i, [vp, i, ctypes.POINTER(i), vp, vp, vp, vp, vp, vp]),
+        "fcm_batch_apply_stages": (i, [vp, i, ctypes.POINTER(i), vp, vp, vp, vp, vp, i, vp]),
+        "fcm_max_systems": (i, [vp]),
         "fcm_destroy": (i, [vp]),
         "fcm_apply": (i, [vp, i, vp, vp, vp, vp, vp, vp]),
         "fcm_apply_stages": (i, [vp, i, vp, vp, vp, vp, vp, i, vp]),
@@ -66,6 +95,13 @@ def _load():
         "fcm_cutoff_radius": (i, [d, d, d, d, d, i, ctypes.POINTER(d)]),
         "fcm_pair_correction_noalloc": (i, [ctypes.POINTER(Params), i, vp, vp, vp, vp, vp, vp]),
         "fcm_last_error": (ctypes.c_char_p, []),
+        "fcm_server_create": (i, [i, sz, i, ctypes.POINTER(vp)]),
+        "fcm_server_submit": (i, [vp, ctypes.POINTER(Request), ctypes.POINTER(ll)]),
+        "fcm_server_poll": (i, [vp, ll, ll, ctypes.POINTER(i)]),
+        "fcm_server_cancel": (i, [vp, ll]),
+        "fcm_server_get_stats": (i, [vp, ctypes.POINTER(ServerStats)]),
+        "fcm_server_reset_latency": (i, [vp]),
+        "fcm_server_destroy": (i, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -78,8 +114,13 @@ _lib = _load()
 
 #: symbols declared in include/fcm.h, for the export check
 EXPORTED = ("fcm_version", "fcm_params_default", "fcm_create", "fcm_destroy", "fcm_apply", "fcm_apply_stages",
-            "fcm_spread", "fcm_copy_grid", "fcm_check", "fcm_set_timing", "fcm_read_timing", "fcm_launch_count",
-            "fcm_workspace_bytes", "fcm_cutoff_radius", "fcm_pair_correction_noalloc", "fcm_last_error")
+            "fcm_create_batch", "fcm_batch_apply", "fcm_batch_apply_stages", "fcm_max_systems", "fcm_spread", "fcm_copy_grid", "fcm_check", "fcm_set_timing", "fcm_read_timing", "fcm_launch_count",
+            "fcm_workspace_bytes", "fcm_cutoff_radius", "fcm_pair_correction_noalloc", "fcm_last_error",
+            "fcm_server_create", "fcm_server_submit", "fcm_server_poll", "fcm_server_cancel", "fcm_server_get_stats",
+            "fcm_server_reset_latency", "fcm_server_destroy")
+
+#: most systems of one batched pass (include/fcm.h)
+MAX_BATCH = 1024
 
 #: capacity of fcm_pair_correction_noalloc's fixed scratch (include/fcm.h)
 NOALLOC_MAX_N = 65536
@@ -133,11 +174,12 @@ def _ptr(x) -> int | None:
 class Handle:
     """One periodic system's workspace on one GPU (fcm_create / fcm_destroy)."""
 
-    def __init__(self, params: Params, device: int = 0):
+    def __init__(self, params: Params, device: int = 0, max_systems: int = 1):
         self._h = ctypes.c_void_p()
-        _check(_lib.fcm_create(ctypes.byref(params), int(device), ctypes.byref(self._h)))
+        _check(_lib.fcm_create_batch(ctypes.byref(params), int(max_systems), int(device), ctypes.byref(self._h)))
         self.params = params
         self.device = device
+        self.max_systems = int(max_systems)
 
     def close(self):
         if self._h:
@@ -166,6 +208,13 @@ class Handle:
     def apply_stages(self, n, pos, F, T, U, W, stages, stream=0):
         _check(_lib.fcm_apply_stages(self._h, int(n), _ptr(pos), _ptr(F), _ptr(T), _ptr(U), _ptr(W), int(stages),
                                      stream or None))
+
+    def batch_apply(self, offsets, pos, F, T, U, W, stream=0, stages=STAGE_ALL):
+        """Stacked systems: system s owns rows offsets[s] .. offsets[s+1]-1 (host sequence of ints)."""
+        n_sys = len(offsets) - 1
+        arr = (ctypes.c_int * max(len(offsets), 1))(*[int(v) for v in offsets])
+        _check(_lib.fcm_batch_apply_stages(self._h, int(n_sys), arr, _ptr(pos), _ptr(F), _ptr(T), _ptr(U), _ptr(W),
+                                           int(stages), stream or None))
 
     def spread(self, n, pos, F, T, stream=0):
         _check(_lib.fcm_spread(self._h, int(n), _ptr(pos), _ptr(F), _ptr(T), stream or None))
@@ -224,3 +273,99 @@ def apply_tensors(handle: Handle, pos, F, T=None, U=None, W=None, want_W=True, s
         W = torch.empty_like(F)
     handle.apply_stages(n, pos, F, T, U, W, stages, _stream_of(stream))
     return U, W
+
+
+# ---- serving engine ------------------------------------------------------------------
+
+class Ticket:
+    """A submitted request: its id and the host arrays the server reads and writes."""
+
+    def __init__(self, rid, arrays, U, W):
+        self.id = rid
+        self._arrays = arrays   # keeps inputs alive until the request is done
+        self.U = U
+        self.W = W
+        self.status = None
+
+
+class Server:
+    """fcm_server_*: requests of any size and box from any thread, batched per grid class on one GPU.
+
+    ``submit`` takes C-contiguous numpy arrays of shape (n, 3) (float32 for FCM_FP32 parameters,
+    float64 for FCM_FP64) and returns a Ticket whose U (and W) arrays hold the result once ``wait``
+    reports it done."""
+
+    def __init__(self, device=0, hbm_budget=8 << 30, max_batch=64):
+        self._s = ctypes.c_void_p()
+        _check(_lib.fcm_server_create(int(device), int(hbm_budget), int(max_batch), ctypes.byref(self._s)))
+
+    def close(self):
+        if self._s:
+            _check(_lib.fcm_server_destroy(self._s))
+            self._s = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def submit(self, params: Params, pos, F, T=None, want_W=True) -> Ticket:
+        import numpy as np
+        dt = np.float64 if params.precision == FCM_FP64 else np.float32
+        arrs = []
+        for a in (pos, F, T):
+            if a is None:
+                arrs.append(None)
+                continue
+            a = np.ascontiguousarray(a, dtype=dt)
+            if a.ndim != 2 or a.shape[1] != 3:
+                raise ValueError("pos, F, T must have shape (n, 3)")
+            arrs.append(a)
+        n = arrs[0].shape[0]
+        U = np.empty((n, 3), dtype=dt)
+        W = np.empty((n, 3), dtype=dt) if (want_W or T is not None) else None
+        r = Request()
+        r.params = params
+        r.n = n
+        r.pos, r.F = arrs[0].ctypes.data, arrs[1].ctypes.data
+        r.T = arrs[2].ctypes.data if arrs[2] is not None else None
+        r.U = U.ctypes.data
+        r.W = W.ctypes.data if W is not None else None
+        rid = ctypes.c_longlong()
+        _check(_lib.fcm_server_submit(self._s, ctypes.byref(r), ctypes.byref(rid)))
+        return Ticket(rid.value, arrs, U, W)
+
+    def wait(self, t: Ticket, timeout_s: float = 60.0) -> bool:
+        """True once done (t.status holds its result code), False if still running after timeout_s."""
+        if t.status is not None:
+            return True
+        st = ctypes.c_int()
+        code = _lib.fcm_server_poll(self._s, t.id, int(timeout_s * 1e6), ctypes.byref(st))
+        if code == FCM_ERR_TIMEOUT:
+            return False
+        _check(code)
+        t.status = st.value
+        return True
+
+    def cancel(self, t: Ticket) -> bool:
+        """True if removed before launch, False if it already launched."""
+        code = _lib.fcm_server_cancel(self._s, t.id)
+        if code == FCM_ERR_BUSY:
+            return False
+        _check(code)
+        return True
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(_lib.fcm_server_get_stats(self._s, ctypes.byref(st)))
+        return {name: getattr(st, name) for name, _ in ServerStats._fields_}
+
+    def reset_latency(self):
+        _check(_lib.fcm_server_reset_latency(self._s))

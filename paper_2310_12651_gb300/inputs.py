@@ -92,10 +92,19 @@ def random_rods(n_rods: int, per_rod: int, L: float, seed: int, bond: float = 2.
     are drawn with axes inside a cone around z (cos theta >= ``cone_cos``), which
     packs. Returns (positions wrapped into [0, L), the volume fraction reached
     with radius 1 spheres); ``random_rods.last_stats`` records how many rods were
-    isotropic and how many aligned.
+    isotropic and how many aligned. ``min_sep <= 0`` skips the rejection (rods may
+    cross), for workloads where only the layout's clustering matters.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     offs = (np.arange(per_rod) - 0.5 * (per_rod - 1)) * bond
+    if min_sep <= 0:   # no rejection: rods may cross each other (spheres within a rod stay bond apart)
+        c = rng.random((n_rods, 3)) * L
+        v = rng.normal(size=(n_rods, 3))
+        v /= np.linalg.norm(v, axis=1, keepdims=True)
+        pos = np.mod(c[:, None, :] + offs[None, :, None] * v[:, None, :], L).reshape(-1, 3)
+        pos = np.minimum(pos, np.nextafter(L, 0))
+        random_rods.last_stats = {"isotropic": n_rods, "aligned": 0, "attempts": n_rods}
+        return pos, pos.shape[0] * 4.0 * math.pi / 3.0 / L ** 3
     accepted: list[np.ndarray] = []
     tree = None
     pending: list[np.ndarray] = []

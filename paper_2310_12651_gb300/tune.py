@@ -115,7 +115,8 @@ def grid_for(L: float, Sigma: float, ratio: float) -> int:
     return m
 
 
-def candidates(n: int, L: float, tol: float, torques: bool = True, a: float = 1.0, max_grid: int = 512):
+def candidates(n: int, L: float, tol: float, torques: bool = True, a: float = 1.0, max_grid: int = 512,
+               min_grid: int = 8):
     """Every admissible parameter set on the Sigma/sigma ladder, with its modelled cost (seconds)."""
     sg = a / SQRT_PI
     ratio = resolution_for(GRID_SHARE * tol)
@@ -127,7 +128,7 @@ def candidates(n: int, L: float, tol: float, torques: bool = True, a: float = 1.
         standard = s == 1.0
         # standard FCM resolves the narrower rotlet width sigma_D when torques act
         width = min(Sigma, SIGMA_D_STANDARD * a) if (standard and torques) else Sigma
-        M = grid_for(L, width, ratio)
+        M = max(grid_for(L, width, ratio), grid_for(L, L, min_grid))
         if M > max_grid:
             continue
         h = L / M
@@ -137,7 +138,8 @@ def candidates(n: int, L: float, tol: float, torques: bool = True, a: float = 1.
         rc = 0.0 if standard else pair_cutoff(Sigma, tol, rho, torques)
         if rc > 0.5 * L:
             continue
-        m = max(int(L / rc), 3) if rc > 0 else 0
+        # pair cells as the library builds them: side max(r_c, (8 / rho)^(1/3)), at least 3 per side
+        m = max(int(L / max(rc, (8.0 / rho) ** (1.0 / 3.0))), 3) if rc > 0 else 0
         cand = 27.0 * rho * (L / m) ** 3 if m else 0.0
         cost = (COST["point"] * n * MG ** 3 + COST["candidate"] * n * cand + COST["grid"] * M ** 3
                 + COST["fixed"])
@@ -147,10 +149,11 @@ def candidates(n: int, L: float, tol: float, torques: bool = True, a: float = 1.
     return out
 
 
-def choose(n: int, L: float, tol: float = 1e-5, torques: bool = True, measure=None, top: int = 3):
+def choose(n: int, L: float, tol: float = 1e-5, torques: bool = True, measure=None, top: int = 3,
+           max_grid: int = 512, min_grid: int = 8):
     """Best parameter set for a system. ``measure(params) -> seconds`` (optional) times the ``top``
     candidates of the cost model and keeps the fastest."""
-    cands = candidates(n, L, tol, torques)
+    cands = candidates(n, L, tol, torques, max_grid=max_grid, min_grid=min_grid)
     if not cands:
         raise ValueError("no admissible fast-FCM parameters for this system")
     if measure is None:

@@ -76,3 +76,42 @@ def test_cutoff_rule_matches_oracle(fcm, Sigma, tol, torques):
 
 def test_last_error_is_a_message(fcm):
     assert isinstance(fcm.library().fcm_last_error(), bytes)
+
+
+@pytest.mark.parametrize("max_systems", [0, -3, 1025])
+def test_batch_handle_rejects_bad_system_counts(fcm, max_systems):
+    p = fcm.make_params(L=100.0, M=64, Sigma=2.0, r_c=16.9, M_G=12, max_n=10)
+    with pytest.raises(fcm.FcmError) as e:
+        fcm.Handle(p, max_systems=max_systems)
+    assert e.value.code == fcm.FCM_ERR_ARG and "max_systems" in str(e.value)
+
+
+def _struct_fields(name):
+    text = open(os.path.join(ROOT, "include", "fcm.h")).read()
+    body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (name, name), text, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        parts = [p.strip().lstrip("*") for p in decl.split(",")]
+        first = parts[0].split()[-1].lstrip("*")
+        names.append(first)
+        names.extend(parts[1:])
+    return names
+
+
+def test_server_structs_match_header(fcm):
+    assert _struct_fields("fcm_request") == [f[0] for f in fcm.Request._fields_]
+    assert _struct_fields("fcm_server_stats") == [f[0] for f in fcm.ServerStats._fields_]
+    assert ctypes.sizeof(fcm.Request) == 112 + 8 + 5 * 8
+    assert ctypes.sizeof(fcm.ServerStats) == 10 * 8 + 2 * 8 + 3 * 8
+
+
+@pytest.mark.parametrize("budget, max_batch, message", [(0, 4, "hbm_budget"), (1 << 30, 0, "max_batch"),
+                                                        (1 << 30, 5000, "max_batch")])
+def test_server_rejects_bad_arguments_on_the_host(fcm, budget, max_batch, message):
+    with pytest.raises(fcm.FcmError) as e:
+        fcm.Server(hbm_budget=budget, max_batch=max_batch)
+    assert e.value.code == fcm.FCM_ERR_ARG and message in str(e.value)

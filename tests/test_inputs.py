@@ -1,9 +1,12 @@
 """The seeded workload generators: reproducible, non-overlapping, the stated shapes."""
 import math
+import os
 
 import numpy as np
 
 from paper_2310_12651_gb300 import inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _min_periodic_distance(Y, L):
@@ -45,3 +48,27 @@ def test_random_rods_geometry():
     d = Y[1:8] - Y[0:7]
     d -= L * np.round(d / L)
     np.testing.assert_allclose(np.linalg.norm(d, axis=1), 2.2, atol=1e-9)
+
+
+def test_rods_without_rejection_keep_their_bonds():
+    L = 50.0
+    pos, phi = inputs.random_rods(100, 64, L, 3, min_sep=0.0)
+    assert pos.shape == (6400, 3) and np.all(pos >= 0) and np.all(pos < L)
+    d = np.diff(pos.reshape(100, 64, 3), axis=1)
+    d -= L * np.round(d / L)
+    assert np.allclose(np.linalg.norm(d, axis=2), 2.2)
+    assert abs(phi - 6400 * 4 * np.pi / 3 / L ** 3) < 1e-12
+
+
+def test_serving_pool_shares_parameters_within_a_class():
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    pool, classes = bench.serve_pool(pool=8)
+    assert len(pool) == 8 and sum(s["rods"] for s in pool) == 4
+    for s in pool:
+        L, ch = classes[s["cls"]]
+        assert s["L"] == L and 2000 <= s["n"] <= 200000 + 64
+        assert s["params"].M[0] == ch["M"] and 32 <= ch["M"] <= 256
+        assert s["n"] * 4 * np.pi / 3 / L ** 3 <= 0.2 + 1e-9
+        assert all(a.dtype == np.float32 and a.shape == (s["n"], 3) for a in s["arrays"])
