@@ -233,6 +233,65 @@ def paper_sweep(device, reps=5, warmup=3, full=False):
             "paper_peak_ptps": PAPER_PEAK_PTPS, "paper_hardware": "RTX 2080 Ti, FP32", "rows": rows}
 
 
+def rods_bench(device, systems=8, steps=5, warmup=3, tol=1e-4):
+    """The filament layout (clustered, uneven pair load): 1,024 rods x 64 spheres per system at 5%
+    (bond 2.2a, centres uniform, axes isotropic, rods may cross), F = (0,0,-1) + 0.1 N(0,1) per sphere,
+    T = 0.1 N(0,1); 128^3 grid with Sigma, M_G and R_c from the autotuner at tol; one batched pass over
+    `systems` systems per step; FP32 error against the FP64 plain path on system 0."""
+    import numpy as np
+    import torch
+    from paper_2310_12651_gb300 import fcm, inputs, tune
+    n = 65536
+    L = inputs.box_edge(n, 0.05)
+    ch = tune.choose(n, L, tol, torques=True, grid=128)
+    dev = torch.device("cuda", device)
+    stream = torch.cuda.current_stream(dev)
+    Ys, Fs, Ts = [], [], []
+    for b in range(systems):
+        Y, _ = inputs.random_rods(1024, 64, L, 2310127100 + b, min_sep=0.0)
+        F, T = inputs.random_loads(n, 2310127200 + b, scale=0.1, mean_free=False, bias=(0.0, 0.0, -1.0))
+        Ys.append(Y)
+        Fs.append(F)
+        Ts.append(T)
+    pos, F, T = (torch.as_tensor(np.concatenate(a), dtype=torch.float32, device=dev) for a in (Ys, Fs, Ts))
+    U = torch.empty_like(F)
+    W = torch.empty_like(F)
+    offsets = [b * n for b in range(systems + 1)]
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    p = tune.make_params(ch, L, n * systems)
+    with fcm.Handle(p, device, max_systems=systems) as h:
+        for _ in range(warmup):
+            h.batch_apply(offsets, pos, F, T, U, W, stream.cuda_stream)
+        ms = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h.batch_apply(offsets, pos, F, T, U, W, stream.cuda_stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+        h.set_timing(True)
+        h.read_timing()
+        h.batch_apply(offsets, pos, F, T, U, W, stream.cuda_stream)
+        stages = {k: round(v[0], 4) for k, v in h.read_timing().items() if v[1]}
+        h.set_timing(False)
+        assert h.check() == 0
+    p64 = tune.make_params(ch, L, n, precision=fcm.FCM_FP64)
+    with fcm.Handle(p64, device) as h64:
+        U64 = torch.empty((n, 3), dtype=torch.float64, device=dev)
+        W64 = torch.empty_like(U64)
+        h64.apply(n, pos[:n].double(), F[:n].double(), T[:n].double(), U64, W64, stream.cuda_stream)
+        torch.cuda.synchronize()
+    eu = float(torch.linalg.norm(U[:n].double() - U64) / torch.linalg.norm(U64))
+    ew = float(torch.linalg.norm(W[:n].double() - W64) / torch.linalg.norm(W64))
+    return {"workload": f"{systems} systems x 1,024 rods x 64 spheres, phi = 5% (L = {L:.2f}a), rods may cross, "
+                        f"F = (0,0,-1) + 0.1 N(0,1), T = 0.1 N(0,1), 128^3, autotuned at tol {tol:g}",
+            "Sigma_over_sigma": ch["Sigma_over_sigma"], "M_G": ch["M_G"], "r_c": ch["r_c"],
+            "ms_per_step": ms / steps, "particle_applies_per_s": n * systems * steps / (ms * 1e-3),
+            "stage_ms_one_pass": stages, "fp32_rel_l2_vs_fp64": {"U": eu, "W": ew}}
+
+
 SERVE_CLASSES = 8          # box-size ladder of the serving mix (log-spaced L, one grid class each)
 SERVE_POOL = 32            # distinct systems drawn for the mix (half spheres, half 64-sphere rods)
 
@@ -381,8 +440,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--spread-kernel", type=int, default=0, help="0 choose, 1 row-stationary, 2 shared atomics")
+    ap.add_argument("--tile", default="0,0,0", help="spread/gather tile x,y,z in grid points (0,0,0: the library's choice)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-mix measurement")
     ap.add_argument("--no-sweep", action="store_true", help="skip the paper-settings PTPS sweep")
+    ap.add_argument("--no-rods", action="store_true", help="skip the filament-layout measurement")
     ap.add_argument("--sweep-full", action="store_true", help="include the 12.8%% (N = 1.96M) sweep row")
     ap.add_argument("--serve-requests", type=int, default=1024)
     ap.add_argument("--mode", default="batched", choices=["batched", "single"],
@@ -410,8 +471,9 @@ def main():
     B = args.batch or WORKLOADS[args.workload]["batch"]
     n = w["n"]
     batched = args.mode == "batched"
+    tile = tuple(int(v) for v in args.tile.split(","))
     params = fcm.make_params(w["L"], w["M"], w["Sigma"], w["r_c"], w["M_G"], n * B if batched else n, fcm.FCM_FP32,
-                             spread_kernel=args.spread_kernel)
+                             spread_kernel=args.spread_kernel, tile=tile)
     h = fcm.Handle(params, local, max_systems=B if batched else 1)
     Ys, Fs, Ts = [], [], []
     for b in range(B):
@@ -556,6 +618,7 @@ def main():
     if not args.no_serve:
         serve = serve_bench(local, requests=args.serve_requests)
     sweep = None if args.no_sweep else paper_sweep(local, full=args.sweep_full)
+    rods = None if args.no_rods else rods_bench(local)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -572,7 +635,7 @@ def main():
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B * 3 * n * 3 * 4,
                    "d2h_bytes_per_step": B * 2 * n * 3 * 4},
            "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
-           "fp64_plain": fp64, "serve": serve, "paper_sweep": sweep,
+           "fp64_plain": fp64, "serve": serve, "paper_sweep": sweep, "rods": rods,
            "speedup_vs_fp64_plain": (value / world / fp64["value"]) if fp64 else None,
            "stages": stages_out, "step_ms_median": statistics.median(step_ms),
            "workspace_bytes": h.workspace_bytes()}

@@ -116,8 +116,9 @@ def grid_for(L: float, Sigma: float, ratio: float) -> int:
 
 
 def candidates(n: int, L: float, tol: float, torques: bool = True, a: float = 1.0, max_grid: int = 512,
-               min_grid: int = 8):
-    """Every admissible parameter set on the Sigma/sigma ladder, with its modelled cost (seconds)."""
+               min_grid: int = 8, grid: int | None = None):
+    """Every admissible parameter set on the Sigma/sigma ladder, with its modelled cost (seconds).
+    ``grid`` fixes M (then only Sigma values the grid resolves at tol are admissible)."""
     sg = a / SQRT_PI
     ratio = resolution_for(GRID_SHARE * tol)
     c = truncation_for(GRID_SHARE * tol)
@@ -128,7 +129,12 @@ def candidates(n: int, L: float, tol: float, torques: bool = True, a: float = 1.
         standard = s == 1.0
         # standard FCM resolves the narrower rotlet width sigma_D when torques act
         width = min(Sigma, SIGMA_D_STANDARD * a) if (standard and torques) else Sigma
-        M = max(grid_for(L, width, ratio), grid_for(L, L, min_grid))
+        if grid is not None:
+            M = int(grid)
+            if width / (L / M) < ratio:
+                continue
+        else:
+            M = max(grid_for(L, width, ratio), grid_for(L, L, min_grid))
         if M > max_grid:
             continue
         h = L / M
@@ -150,10 +156,10 @@ def candidates(n: int, L: float, tol: float, torques: bool = True, a: float = 1.
 
 
 def choose(n: int, L: float, tol: float = 1e-5, torques: bool = True, measure=None, top: int = 3,
-           max_grid: int = 512, min_grid: int = 8):
+           max_grid: int = 512, min_grid: int = 8, grid: int | None = None):
     """Best parameter set for a system. ``measure(params) -> seconds`` (optional) times the ``top``
     candidates of the cost model and keeps the fastest."""
-    cands = candidates(n, L, tol, torques, max_grid=max_grid, min_grid=min_grid)
+    cands = candidates(n, L, tol, torques, max_grid=max_grid, min_grid=min_grid, grid=grid)
     if not cands:
         raise ValueError("no admissible fast-FCM parameters for this system")
     if measure is None:
