@@ -1,20 +1,16 @@
 // libfcm C-ABI: handle lifetime, parameter checks, workspace, and the launch
 // sequence of one mobility product (Section 4):
 //
-//   caller stream : bin ─► zero grid ─► spread ─┬──────────────────────────────────────┬─► add ─► U, W
-//   high priority :                             ├─► R2C ─► project ─► C2R ─► gather ─┤
-//   side (low)    :                             └─► pair ────────────────────────────┘
+//   caller stream : bin ─► zero grid ─► spread ─┬─► R2C ─► project ─► C2R ─► gather ─┬─► add ─► U, W
+//   side stream   :                             └─► pair ────────────────────────────┘
 //
 // The pair correction only needs the cell-sorted particles. It is forked onto
-// the handle's low-priority side stream after the spread, where it overlaps the
-// latency-bound FFT chain and the gather, which run on the handle's
-// high-priority stream (the spread fills every SM's registers, so overlapping
-// it gains nothing; a gather CTA leaves room for a pair CTA on the same SM).
-// The gather writes the grid part of U and W in input order, the pair kernel
-// its sums, and a small kernel on the caller's stream adds them after the
-// join. Without the pair stage everything runs on the caller's stream. The
-// fork/join uses events only, so a caller may capture fcm_apply into a CUDA
-// graph.
+// the handle's side stream after the spread, where it runs beside the FFT
+// chain and the gather (the spread fills every SM's registers, so overlapping
+// it gains nothing). The gather writes the grid part of U and W in input
+// order, the pair kernel its sums, and a small kernel adds them after the
+// join. The fork/join uses events only, so a caller may capture fcm_apply into
+// a CUDA graph.
 #include <cufft.h>
 
 #include <chrono>
@@ -215,8 +211,7 @@ struct fcm_handle {
   PairConsts<double> pd{};
   PairTable ptab{};
   cudaStream_t side = nullptr;
-  cudaStream_t hi = nullptr;   // high-priority stream of the FFT chain and gather while the pair runs
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_hi = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   BinBuffers bb{};
   void* grid = nullptr;
   void* spec = nullptr;
@@ -273,9 +268,7 @@ void release(fcm_handle* h) {
   }
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
-  if (h->ev_hi) cudaEventDestroy(h->ev_hi);
   if (h->side) cudaStreamDestroy(h->side);
-  if (h->hi) cudaStreamDestroy(h->hi);
   for (void* p : h->allocs) cudaFree(p);
   delete h;
 }
@@ -486,14 +479,10 @@ int run(fcm_handle* h, int nsys, int n, const R* pos, const R* F, const R* T, R*
       if ((rc = launch_pair_stage(h, g, bb, n, U, Wout, torque, grid_on, s))) return rc;
     }
     if (!spread_only) {
-      // With the pair stage running, the FFT chain and the gather go to the handle's
-      // high-priority stream (forked from s after the spread, joined before the add), so the
-      // block scheduler serves them first and the pair kernel fills the SMs they leave idle.
+      // FFT chain and gather on the caller's stream, beside the pair kernel on the side stream.
+      // (Giving them a higher stream priority than the pair made the step slower: the pair then
+      // ran mostly after the gather instead of beside the FFT.)
       cudaStream_t m = s;
-      if (pair_on) {
-        m = h->hi;
-        FCM_CUDA(cudaStreamWaitEvent(m, h->ev_fork, 0));   // ev_fork: recorded on s after the spread
-      }
       if ((rc = stage_begin(h, 2, m, &t_fft))) return rc;
       FCM_CUFFT(cufftSetStream(plan->r2c, m));
       FCM_CUFFT(cufftSetStream(plan->c2r, m));
@@ -519,8 +508,6 @@ int run(fcm_handle* h, int nsys, int n, const R* pos, const R* F, const R* T, R*
       if ((rc = stage_end(h, t_gather, m))) return rc;
       FCM_CUDA(cudaGetLastError());
       if (pair_on) {
-        FCM_CUDA(cudaEventRecord(h->ev_hi, m));
-        FCM_CUDA(cudaStreamWaitEvent(s, h->ev_hi, 0));
         FCM_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
         launch_add<R>(U, (const R*)h->upair, Wout, (const R*)h->wpair, 3 * (size_t)n, s, &h->launches);
         FCM_CUDA(cudaGetLastError());
@@ -760,13 +747,9 @@ int fcm_create_batch(const fcm_params* p, int max_systems, int device, fcm_handl
   cudaError_t ce = cudaMemset(b.tile_count, 0, 4 * (size_t)(b.ntiles + 1));
   if (ce == cudaSuccess) ce = cudaMemset(b.cell_count, 0, 4 * (size_t)(b.ncells + 1));
   if (ce == cudaSuccess) ce = cudaMemset(b.status, 0, 256);
-  int prio_least = 0, prio_greatest = 0;
-  if (ce == cudaSuccess) ce = cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
-  if (ce == cudaSuccess) ce = cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, prio_least);
-  if (ce == cudaSuccess) ce = cudaStreamCreateWithPriority(&h->hi, cudaStreamNonBlocking, prio_greatest);
+  if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
   if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
   if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
-  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&h->ev_hi, cudaEventDisableTiming);
   if (ce != cudaSuccess) { release(h); return fail(FCM_ERR_CUDA, std::string("setup: ") + cudaGetErrorString(ce)); }
   // One R2C and one C2R plan per bucket of systems (3 transforms per system), all with one work
   // area of the largest size any of them needs.
