@@ -87,11 +87,16 @@ __device__ inline int window_start_scaled(R s, int MG) {
   v = v < R(-(1 << 29)) ? R(-(1 << 29)) : (v > R(1 << 29) ? R(1 << 29) : v);
   return (int)v + 1;
 }
+// a[d] for a runtime d by selects: indexing a kernel-parameter array with a runtime index
+// makes the compiler copy the whole parameter block to local memory.
+template <typename T>
+__host__ __device__ inline T sel3(const T (&a)[3], int d) { return d == 0 ? a[0] : (d == 1 ? a[1] : a[2]); }
+
 __device__ inline int window_start_d(const Geometry<float>& g, int d, float y) {
-  return window_start_scaled(y * g.inv_h[d], g.MG);
+  return window_start_scaled(y * sel3(g.inv_h, d), g.MG);
 }
 __device__ inline int window_start_d(const Geometry<double>& g, int d, double y) {
-  return window_start_scaled(y / g.h[d], g.MG);
+  return window_start_scaled(y / sel3(g.h, d), g.MG);
 }
 
 // i mod M for i in (-M, 2M): one correction instead of an integer division.

@@ -88,7 +88,8 @@ __device__ inline int4 window_offset(const Geometry<float>& g, const TileOrigin&
 
 // Copies the extended region of the grid (3 components) into shared memory with
 // asynchronous 4-byte copies: warps take (component, z) planes, lanes take x,
-// rows advance with incremental offsets.
+// rows advance by pointer increments (the y range is split at its periodic wrap,
+// so no per-row wrap test).
 __device__ inline void stage_region_async(const Geometry<float>& g, const TileOrigin& o, const ExtLayout& l,
                                           const float* __restrict__ grid, float* ext) {
   const size_t Mtot = (size_t)g.M[0] * g.M[1] * g.M[2];
@@ -96,18 +97,28 @@ __device__ inline void stage_region_async(const Geometry<float>& g, const TileOr
   if (lane < l.EX) {
     const int gx = wrap_index(o.ox0 + lane, g.M[0]);
     const int gy0 = wrap_index(o.oy0, g.M[1]);
+    const int n1 = min(l.EY, g.M[1] - gy0);   // rows before the periodic wrap in y
+    const size_t row = (size_t)g.M[0];
     for (int pl = warp; pl < 3 * l.EZ; pl += nwarp) {
       const int c = pl / l.EZ;
       const int ez = pl - c * l.EZ;
       const int gz = wrap_index(o.oz0 + ez, g.M[2]);
       const float* gplane = grid + c * Mtot + (size_t)gz * g.M[1] * g.M[0] + gx;
-      const unsigned sbase = (unsigned)__cvta_generic_to_shared(ext + c * l.C + ez * l.Q + lane);
-      int gy = gy0;
-      for (int ey = 0; ey < l.EY; ++ey) {
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sbase + 4u * (unsigned)(ey * l.P)),
-                     "l"(gplane + (size_t)gy * g.M[0])
-                     : "memory");
-        gy = (gy + 1 == g.M[1]) ? 0 : gy + 1;
+      unsigned sa = (unsigned)__cvta_generic_to_shared(ext + c * l.C + ez * l.Q + lane);
+      const unsigned sstep = 4u * (unsigned)l.P;
+      // rows gy0 .. gy0 + n1 - 1, then rows 0 .. EY - n1 - 1: pointers advance by one row each
+      const float* src = gplane + (size_t)gy0 * row;
+#pragma unroll 4
+      for (int ey = 0; ey < n1; ++ey) {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(src) : "memory");
+        sa += sstep;
+        src += row;
+      }
+      src = gplane;
+      for (int ey = n1; ey < l.EY; ++ey) {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(src) : "memory");
+        sa += sstep;
+        src += row;
       }
     }
   }

@@ -78,9 +78,9 @@ __device__ inline void eval_pair(const PairConsts<float>& pc, const PairTable& t
 // loads instead of L2 traffic repeated for every particle of the cell.
 
 constexpr int kCellWarps = 8;
-constexpr int kCandChunk = 1536;
+constexpr int kCandChunk = 1024;
 static_assert(kCandChunk % 64 == 0, "candidate chunks are padded to whole 64-candidate passes");
-constexpr int kIBatch = 256;
+constexpr int kIBatch = 128;
 constexpr int kMaxPieces = 18;
 
 template <bool TORQUE>
@@ -97,7 +97,7 @@ __device__ inline void neu_add(float* s, float* c, float v) {
 }
 
 template <bool TORQUE, bool SHIFT>
-__global__ void __launch_bounds__(kCellWarps * 32, 2) pair_cell_kernel(Geometry<float> g, PairConsts<float> pc,
+__global__ void __launch_bounds__(kCellWarps * 32, 3) pair_cell_kernel(Geometry<float> g, PairConsts<float> pc,
                                                                        PairTable tab,
                                                                        const float4* __restrict__ cpos,
                                                                        const float4* __restrict__ cF,

@@ -31,7 +31,7 @@ __device__ inline void fill_tables(const Geometry<double>& g, const KernelConsts
   for (int k = threadIdx.x; k < 3 * g.MG; k += blockDim.x) {
     const int d = k / g.MG, j = k - d * g.MG;
     const double yd = d == 0 ? y.x : (d == 1 ? y.y : y.z);
-    const double dd = (double)(t.i0[d] + j) * g.h[d] - yd;
+    const double dd = (double)(t.i0[d] + j) * sel3(g.h, d) - yd;
     t.d[d][j] = dd;
     t.gS[d][j] = exp(-dd * dd * kc.inv2S2);
     t.gD[d][j] = exp(-dd * dd * kc.inv2SD2);

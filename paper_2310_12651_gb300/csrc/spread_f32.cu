@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(rows_threads(MGT), 1) spread_rows_kernel(Geome
       const int j = rem - d * MGT;
       const float4 y = pos[base + q];
       const float yd = d == 0 ? y.x : (d == 1 ? y.y : y.z);
-      const float h = g.h[d];
+      const float h = sel3(g.h, d);
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
       if (j < MG) {
         const float dd = (float)(window_start_d(g, d, yd) + j) * h - yd;
