@@ -51,7 +51,7 @@ WORKLOADS = {
 }
 # dram__bytes_read.sum + dram__bytes_write.sum per system of a launch (cold caches), from one ncu capture of
 # the current kernels; a launch over B systems moves B times this. None once a kernel changes after the capture.
-TRAFFIC_BYTES = {"c2": {"gather": None, "spread": None, "pair": None}}
+TRAFFIC_BYTES = {"c2": {"spread": 28.78e6, "gather": 26.59e6, "pair": 3.18e6}}
 
 
 def workload(name="c2", n=None, h_ref=None):
@@ -292,6 +292,71 @@ def rods_bench(device, systems=8, steps=5, warmup=3, tol=1e-4):
             "stage_ms_one_pass": stages, "fp32_rel_l2_vs_fp64": {"U": eu, "W": ew}}
 
 
+def crossover_study(device, a_over_L=(0.012, 0.008), tols=(1e-4, 1e-6),
+                    phis=(0.005, 0.01, 0.02, 0.04, 0.08, 0.12, 0.16, 0.2), reps=5, warmup=3):
+    """Fast FCM against standard FCM (Sigma = sigma, Sigma_D = sigma_D, no pair correction) on the
+    paper's crossover study shape (Section 5.3, Fig. 3): forces only, one system per apply, each
+    method with the autotuner's parameters for the tolerance (fast FCM: the three cheapest Sigma
+    candidates timed on the GPU, the fastest kept). Returns per point the two times and their ratio,
+    and per (a/L, tol) the volume fraction where the ratio crosses 1 (linear in log phi)."""
+    import numpy as np
+    import torch
+    from paper_2310_12651_gb300 import fcm, inputs, tune
+    dev = torch.device("cuda", device)
+    stream = torch.cuda.current_stream(dev)
+    rows, crossings = [], []
+    systems = {}
+    for aL in a_over_L:
+        L = 1.0 / aL
+        for tol in tols:
+            ratios = []
+            for phi in phis:
+                n = int(round(phi * L ** 3 / (4.0 * math.pi / 3.0)))
+                if (aL, phi) not in systems:
+                    Y = inputs.random_suspension(n, L, 2310127300 + n, min_sep=2.0, max_rounds=400)
+                    F, _ = inputs.random_loads(n, 2310127301 + n, torques=False)
+                    systems[(aL, phi)] = tuple(torch.as_tensor(a, dtype=torch.float32, device=dev) for a in (Y, F))
+                pos, Fd = systems[(aL, phi)]
+                U = torch.empty_like(Fd)
+
+                def timed(choice):
+                    with fcm.Handle(tune.make_params(choice, L, n), device) as h:
+                        for _ in range(warmup):
+                            h.apply(n, pos, Fd, None, U, None, stream.cuda_stream)
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        for _ in range(reps):
+                            h.apply(n, pos, Fd, None, U, None, stream.cuda_stream)
+                        e1.record(stream)
+                        e1.synchronize()
+                        return e0.elapsed_time(e1) * 1e-3 / reps
+
+                cands = tune.candidates(n, L, tol, torques=False, max_grid=512)
+                std = [c for c in cands if c["Sigma_over_sigma"] == 1.0]
+                fast = [c for c in cands if c["Sigma_over_sigma"] != 1.0][:3]
+                if not std or not fast:
+                    continue
+                t_std = timed(std[0])
+                best = min(((timed(c), c) for c in fast), key=lambda x: x[0])
+                ratio = t_std / best[0]
+                ratios.append((phi, ratio))
+                rows.append({"a_over_L": aL, "tol": tol, "phi": phi, "N": n,
+                             "fast": {"Sigma_over_sigma": best[1]["Sigma_over_sigma"], "M": best[1]["M"],
+                                      "M_G": best[1]["M_G"], "r_c": round(best[1]["r_c"], 2), "ms": best[0] * 1e3},
+                             "standard": {"M": std[0]["M"], "M_G": std[0]["M_G"], "ms": t_std * 1e3},
+                             "speedup_fast_over_standard": ratio})
+                print(json.dumps(rows[-1]), flush=True)
+            phi_c = None
+            for (p0, r0), (p1, r1) in zip(ratios, ratios[1:]):
+                if r0 >= 1.0 > r1:
+                    f = (1.0 - r0) / (r1 - r0)
+                    phi_c = math.exp(math.log(p0) + f * (math.log(p1) - math.log(p0)))
+                    break
+            crossings.append({"a_over_L": aL, "tol": tol, "phi_c": phi_c,
+                              "paper_fit_phi_c": -9.24 * aL + 0.22})
+    return {"rows": rows, "crossings": crossings}
+
+
 SERVE_CLASSES = 8          # box-size ladder of the serving mix (log-spaced L, one grid class each)
 SERVE_POOL = 32            # distinct systems drawn for the mix (half spheres, half 64-sphere rods)
 
@@ -395,6 +460,8 @@ def serve_bench(device, requests=1024, loads=(0.5, 0.9), seed=2310126950):
                                      "mean_batch": (st["batched_requests"] - b0["batched_requests"]) /
                                                    max(1, st["batches"] - b0["batches"])})
         st = srv.stats()
+        out["graph_passes"] = st["graph_passes"]
+        out["passes"] = st["batches"]
         out["handles_created"] = st["handles_created"]
         out["handles_evicted"] = st["handles_evicted"]
         out["hbm_bytes"] = st["hbm_bytes"]
@@ -441,6 +508,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--spread-kernel", type=int, default=0, help="0 choose, 1 row-stationary, 2 shared atomics")
     ap.add_argument("--tile", default="0,0,0", help="spread/gather tile x,y,z in grid points (0,0,0: the library's choice)")
+    ap.add_argument("--study", default=None, choices=["crossover"],
+                    help="run a study instead of the bench line: crossover = fast vs standard FCM against phi")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-mix measurement")
     ap.add_argument("--no-sweep", action="store_true", help="skip the paper-settings PTPS sweep")
     ap.add_argument("--no-rods", action="store_true", help="skip the filament-layout measurement")
@@ -464,6 +533,10 @@ def main():
     from paper_2310_12651_gb300 import fcm, inputs
 
     torch.cuda.set_device(local)
+    if args.study == "crossover":
+        if rank == 0:
+            print(json.dumps({"study": "crossover", **crossover_study(local)}), flush=True)
+        return 0
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     sptr = stream.cuda_stream

@@ -208,8 +208,13 @@ int fcm_cutoff_radius(double Sigma, double Sigma_D, double a, double eta, double
  *     stay within hbm_budget: idle handles are evicted least recently used
  *     first; a request whose handle alone would exceed it fails with
  *     FCM_ERR_OOM (admission control).
- *   - Two launch slots (own stream, pinned staging) overlap one pass's copies
- *     and kernels with the next pass's.
+ *   - Four launch slots (own stream, pinned staging) let passes overlap: one
+ *     pass's copies and kernels run beside the next ones'.
+ *   - FP32 passes are captured once per (cached handle, power-of-two bucket of
+ *     systems, staging set) into a CUDA graph and replayed (each handle has two
+ *     staging sets, used alternately): the pass reads its offsets and
+ *     particle count from device memory, so one graph serves every batch that
+ *     fits the bucket and the handle's capacity.
  *   - One worker thread issues all GPU work; submit/poll/cancel/stats may be
  *     called from any thread, fcm_server_destroy from one thread after all
  *     other calls have returned. */
@@ -232,6 +237,7 @@ typedef struct fcm_server_stats {
   long long batches;           /* passes launched                                    */
   long long batched_requests;  /* requests those passes carried                      */
   long long handles_created, handles_evicted;
+  long long graph_passes;      /* passes replayed from a captured CUDA graph         */
   size_t hbm_bytes;            /* device bytes held by cached handles and staging    */
   size_t hbm_budget;
   double latency_p50_us, latency_p99_us, latency_max_us;  /* submit to completion,  */

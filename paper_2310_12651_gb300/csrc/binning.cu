@@ -26,6 +26,7 @@ template <typename R>
 __global__ void __launch_bounds__(256) key_count_kernel(Geometry<R> g, int n, const R* __restrict__ pos,
                                                         BinBuffers b, int need_cells) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b.n_dev) n = min(n, *b.n_dev);
   if (i >= n) return;
   const int sys = system_of(b, i);
   int bad = 0;
@@ -114,6 +115,7 @@ __global__ void __launch_bounds__(256) scatter_kernel(Geometry<R> g, int n, cons
                                                       const R* __restrict__ F, const R* __restrict__ T,
                                                       BinBuffers b, int need_cells) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b.n_dev) n = min(n, *b.n_dev);
   if (i >= n) return;
   int bad = 0;
   Vec4<R> p, f, t;
@@ -167,7 +169,8 @@ void launch_write_offsets(const SysOffsets& o, int n, int* dst, cudaStream_t s, 
 
 template <typename R>
 __global__ void __launch_bounds__(256) add_kernel(R* __restrict__ U, const R* __restrict__ up, R* __restrict__ W,
-                                                  const R* __restrict__ wp, size_t count) {
+                                                  const R* __restrict__ wp, size_t count, const int* n_dev) {
+  if (n_dev) count = min(count, 3 * (size_t)max(*n_dev, 0));
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < count; k += stride) {
     U[k] += up[k];
@@ -176,19 +179,22 @@ __global__ void __launch_bounds__(256) add_kernel(R* __restrict__ U, const R* __
 }
 
 template <typename R>
-void launch_add(R* U, const R* up, R* W, const R* wp, size_t count, cudaStream_t s, long long* launches) {
+void launch_add(R* U, const R* up, R* W, const R* wp, size_t count, cudaStream_t s, long long* launches,
+                const int* n_dev) {
   if (count == 0) return;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const size_t want = (count + 255) / 256;
   const int blocks = (int)(want < (size_t)sms * 8 ? want : (size_t)sms * 8);
-  add_kernel<R><<<blocks, 256, 0, s>>>(U, up, W, wp, count);
+  add_kernel<R><<<blocks, 256, 0, s>>>(U, up, W, wp, count, n_dev);
   *launches += 1;
 }
 
-template void launch_add<float>(float*, const float*, float*, const float*, size_t, cudaStream_t, long long*);
-template void launch_add<double>(double*, const double*, double*, const double*, size_t, cudaStream_t, long long*);
+template void launch_add<float>(float*, const float*, float*, const float*, size_t, cudaStream_t, long long*,
+                                const int*);
+template void launch_add<double>(double*, const double*, double*, const double*, size_t, cudaStream_t, long long*,
+                                 const int*);
 
 __global__ void zero_kernel(uint4* p, size_t n16, unsigned char* tail, size_t ntail) {
   size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;

@@ -170,10 +170,9 @@ void narrow_pair_consts(const PairConsts<double>& in, PairConsts<float>* o) {
 
 int record_error(int code, const char* msg) { return fail(code, msg); }
 
-void build_pair_table(const PairConsts<double>& pd, double r_lo, double r_hi, float4* coef) {
+void build_pair_table(const PairConsts<double>& pd, double r_lo, double r_hi, int n, float4* coef) {
   PairConsts<double> c = pd;
   c.rs2 = 0.0;  // the closed form throughout the tabulated range
-  const int n = kPairTableIntervals;
   const double h = (r_hi - r_lo) / n;
   for (int i = 0; i < n; ++i) {
     double v[4][5];
@@ -446,7 +445,7 @@ const fcm_handle::Plan* plan_for(const fcm_handle* h, int nsys) {
 // with the others, so their transforms stay zero.
 template <typename R>
 int run(fcm_handle* h, int nsys, int n, const R* pos, const R* F, const R* T, R* U, R* W, int stages,
-        bool spread_only, cudaStream_t s) {
+        bool spread_only, cudaStream_t s, const int* n_dev = nullptr) {
   const bool torque = (T != nullptr) || (W != nullptr);
   R* Wout = W ? W : (torque ? (R*)h->wscratch : nullptr);
   const bool grid_on = spread_only || (stages & FCM_STAGE_GRID);
@@ -458,6 +457,7 @@ int run(fcm_handle* h, int nsys, int n, const R* pos, const R* F, const R* T, R*
   g.nsys = nsys;
   bb.nsys = nsys;
   bb.sys_off = nsys > 1 ? h->sys_off : nullptr;
+  bb.n_dev = n_dev;
   bb.ntiles = nsys * g.tiles_per;
   bb.ncells = pair_on ? nsys * g.cells_per : bb.ncells;
   int rc, t_all, t_bin, t_spread, t_fft, t_gather;
@@ -509,7 +509,7 @@ int run(fcm_handle* h, int nsys, int n, const R* pos, const R* F, const R* T, R*
       FCM_CUDA(cudaGetLastError());
       if (pair_on) {
         FCM_CUDA(cudaStreamWaitEvent(s, h->ev_join, 0));
-        launch_add<R>(U, (const R*)h->upair, Wout, (const R*)h->wpair, 3 * (size_t)n, s, &h->launches);
+        launch_add<R>(U, (const R*)h->upair, Wout, (const R*)h->wpair, 3 * (size_t)n, s, &h->launches, n_dev);
         FCM_CUDA(cudaGetLastError());
       }
     }
@@ -586,6 +586,47 @@ int batch_common(fcm_handle* h, int nsys, const int* offsets, const void* pos, c
 }  // namespace
 
 namespace fcm {
+
+// Captures one FP32 batched pass over `bucket` systems (a plan bucket of the handle) into a CUDA
+// graph, for callers that replay the same pass shape many times. Before each replay the caller
+// copies bucket + 1 offsets into handle_sys_off(h) on the replay stream (systems past the real
+// ones repeat the total, so they are empty); the particle kernels read the total from there, and
+// pos/F/T/U/W are the given device addresses (capacity max_n rows each).
+int capture_batch_graph(fcm_handle* h, int bucket, const void* pos, const void* F, const void* T, void* U, void* W,
+                        cudaStream_t s, cudaGraphExec_t* out) {
+  *out = nullptr;
+  if (!h || h->fp64) return fail(FCM_ERR_ARG, "graph capture needs an FP32 handle");
+  const fcm_handle::Plan* plan = plan_for(h, bucket);
+  if (bucket < 1 || bucket > h->max_systems || !plan || plan->systems != bucket)
+    return fail(FCM_ERR_ARG, "bucket must be one of the handle's FFT plan buckets");
+  if (h->timing) return fail(FCM_ERR_ARG, "stage timing is on; graphs are captured without it");
+  DeviceGuard guard(h->device);
+  FCM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  const int rc = run<float>(h, bucket, std::max(h->p.max_n, 1), (const float*)pos, (const float*)F, (const float*)T,
+                            (float*)U, (float*)W, FCM_STAGE_ALL, false, s, h->sys_off + bucket);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(s, &graph);
+  if (e != cudaSuccess || rc != FCM_OK || ee != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    if (rc != FCM_OK) return rc;
+    return fail(FCM_ERR_CUDA, std::string("graph capture failed: ") +
+                                  cudaGetErrorString(e != cudaSuccess ? e : ee));
+  }
+  e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *out = nullptr;
+    return fail(FCM_ERR_CUDA, std::string("graph instantiation failed: ") + cudaGetErrorString(e));
+  }
+  return FCM_OK;
+}
+
+int handle_max_n(const fcm_handle* h) { return h ? h->p.max_n : 0; }
+
+int* handle_sys_off(fcm_handle* h) { return h ? h->sys_off : nullptr; }
 
 // Host checks of fcm_create (without touching a device): parameter ranges and the cutoff rule.
 int check_params(const fcm_params* p, std::string* why) {
@@ -731,18 +772,19 @@ int fcm_create_batch(const fcm_params* p, int max_systems, int device, fcm_handl
   if (!h->fp64 && pairs_on) A(&table, sizeof(float4) * 5 * kPairTableIntervals);
   if (rc != FCM_OK) { std::string e = g_error; release(h); return fail(rc, e); }
   if (table) {
-    std::vector<float4> host(5 * kPairTableIntervals);
+    const int nint = pair_table_intervals(0.5 * sg, std::max(p->r_c, 0.5 * sg + 1e-3), sg);
+    std::vector<float4> host(5 * (size_t)nint);
     const double r_lo = 0.5 * sg;
     const double r_hi = std::max(p->r_c, r_lo + 1e-3);  // below r_lo only the series is used
-    build_pair_table(h->pd, r_lo, r_hi, host.data());
+    build_pair_table(h->pd, r_lo, r_hi, nint, host.data());
     if (cudaMemcpy(table, host.data(), sizeof(float4) * host.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
       release(h);
       return fail(FCM_ERR_CUDA, "copy of the pair table failed");
     }
     h->ptab.coef = (const float4*)table;
     h->ptab.r0 = (float)r_lo;
-    h->ptab.inv_h = (float)(kPairTableIntervals / (r_hi - r_lo));
-    h->ptab.n = kPairTableIntervals;
+    h->ptab.inv_h = (float)(nint / (r_hi - r_lo));
+    h->ptab.n = nint;
   }
   cudaError_t ce = cudaMemset(b.tile_count, 0, 4 * (size_t)(b.ntiles + 1));
   if (ce == cudaSuccess) ce = cudaMemset(b.cell_count, 0, 4 * (size_t)(b.ncells + 1));

@@ -3,6 +3,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <algorithm>
+#include <cmath>
 #include <stdint.h>
 #include <math.h>
 
@@ -210,12 +212,20 @@ __host__ __device__ inline void pair_coeffs(R r2, const PairConsts<R>& C, R& al,
 // kernel: interval i covers r in [r0 + i h, r0 + (i+1) h); coef[5 i + f] holds
 // (c0, c1, c2, c3) of function f (al, bt, cr, gm, dl) in u = (r - r0)/h - i.
 // Built on the host in FP64 from the closed form through four points per interval.
+// The interval count keeps h <= sigma/10 (cubic error below about 1e-7 of each
+// function's largest value), between 64 and kPairTableIntervals: a small table
+// stays in L1, where the per-lane lookups at random r are served.
 constexpr int kPairTableIntervals = 1024;
 struct PairTable {
   const float4* coef;
   float r0, inv_h;
   int n;
 };
+
+__host__ inline int pair_table_intervals(double r_lo, double r_hi, double sigma) {
+  const double n = std::ceil((r_hi - r_lo) / (0.1 * sigma));
+  return (int)std::min(std::max(n, 64.0), (double)kPairTableIntervals);
+}
 
 __device__ inline float cubic(float4 c, float u) { return fmaf(u, fmaf(u, fmaf(u, c.w, c.z), c.y), c.x); }
 
@@ -240,8 +250,8 @@ __device__ inline void pair_coeffs_table(float r2, const PairConsts<float>& C, c
 void make_pair_consts(double a, double eta, double Sigma, double Sigma_D, double r_c,
                       double r_series, PairConsts<double>* out);
 void narrow_pair_consts(const PairConsts<double>& in, PairConsts<float>* out);
-// Fills host memory coef[5 * kPairTableIntervals] (float4 each) for r in [r_lo, r_hi].
-void build_pair_table(const PairConsts<double>& pd, double r_lo, double r_hi, float4* coef);
+// Fills host memory coef[5 * n] (float4 each) for r in [r_lo, r_hi] with n intervals.
+void build_pair_table(const PairConsts<double>& pd, double r_lo, double r_hi, int n, float4* coef);
 
 // ---------------------------------------------------------------- launch API
 // Binning: wraps positions, computes tile and cell keys, counts and ranks,
@@ -257,6 +267,9 @@ struct BinBuffers {
   // Batched launches: particles of system s are rows sys_off[s] .. sys_off[s+1]-1 of the stacked
   // inputs (device array of nsys + 1 ints); nsys <= 1 or sys_off == nullptr is one system.
   const int* sys_off; int nsys;
+  // Non-null for passes replayed from a CUDA graph: the particle count is read here (device) at
+  // run time and the particle kernels are launched for the capacity.
+  const int* n_dev;
 };
 
 // Largest number of systems in one batched pass.
@@ -306,6 +319,7 @@ void launch_zero(void* p, size_t bytes, cudaStream_t s, long long* launches);
 // U[k] += up[k] for k < count, and W[k] += wp[k] when W is non-null (the join of the grid part
 // and the pair sums, both in input order).
 template <typename R>
-void launch_add(R* U, const R* up, R* W, const R* wp, size_t count, cudaStream_t s, long long* launches);
+void launch_add(R* U, const R* up, R* W, const R* wp, size_t count, cudaStream_t s, long long* launches,
+                const int* n_dev = nullptr);   // n_dev: count = 3 * (*n_dev), read on the device
 
 }  // namespace fcm

@@ -15,7 +15,7 @@
 //   * the cache is bounded by an HBM budget: before a new handle is created,
 //     idle handles are evicted least recently used first; a request whose
 //     handle alone exceeds the budget is rejected (FCM_ERR_OOM);
-//   * two launch slots, each with its own stream and pinned staging, so one
+//   * four launch slots, each with its own stream and pinned staging, so one
 //     pass's copies and kernels overlap the next pass's (also across classes);
 //   * every wait is bounded (poll timeouts; the worker polls events).
 //
@@ -41,6 +41,10 @@
 namespace fcm {
 int check_params(const fcm_params* p, std::string* why);
 size_t workspace_estimate(const fcm_params& p, int max_systems);
+int capture_batch_graph(fcm_handle* h, int bucket, const void* pos, const void* F, const void* T, void* U, void* W,
+                        cudaStream_t s, cudaGraphExec_t* out);
+int handle_max_n(const fcm_handle* h);
+int* handle_sys_off(fcm_handle* h);
 }  // namespace fcm
 
 using namespace fcm;
@@ -69,26 +73,41 @@ struct Request {
   Clock::time_point t_submit, t_done;
 };
 
-struct CachedHandle {
-  std::string key;
-  fcm_handle* h = nullptr;
-  int max_systems = 0;
-  int max_n = 0;
-  size_t bytes = 0;
-  cudaEvent_t last = nullptr;   // last pass enqueued on this handle
-  int in_flight = 0;            // slots whose pass uses it
-  unsigned long long last_use = 0;
-};
-
 struct Buffer {
   void* p = nullptr;
   size_t bytes = 0;
 };
 
+// A cached batch handle with two sets of device staging: pos, F, T (and U, W) occupy max_n rows
+// each, so a captured pass sees the same addresses whatever the batch's size. Consecutive passes
+// alternate sets, so one pass's copies overlap the previous pass's kernels; the kernels of passes
+// on one handle are ordered by `computed` (they share its workspace).
+struct CachedHandle {
+  std::string key;
+  fcm_handle* h = nullptr;
+  int max_systems = 0;
+  int max_n = 0;
+  size_t bytes = 0;                 // handle workspace + staging
+  cudaEvent_t computed = nullptr;   // kernels of the last pass enqueued on this handle
+  cudaEvent_t set_free[2] = {nullptr, nullptr};   // staging set no longer read or written
+  int next_set = 0;
+  int in_flight = 0;                // slots whose pass uses it
+  unsigned long long last_use = 0;
+  bool fp32 = true;
+  bool torque = false;
+  size_t rsz = 4;
+  Buffer d_in[2], d_out[2];
+  bool graphs_ok = true;            // cleared if a capture ever fails: direct launches from then on
+  std::map<std::pair<int, int>, cudaGraphExec_t> graphs;   // (bucket, staging set) -> captured pass
+};
+
+// A launch slot: a stream and pinned host staging (pos, F, T, then U, W, each `cap` rows).
 struct Slot {
+  int index = 0;
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
-  Buffer h_in, h_out, d_in, d_out;   // pinned host and device staging
+  Buffer h_in, h_out;                // pinned host staging
+  int* h_off = nullptr;              // pinned offsets copied ahead of a pass
   std::vector<std::shared_ptr<Request>> reqs;
   std::vector<int> offsets;
   CachedHandle* ch = nullptr;
@@ -96,9 +115,10 @@ struct Slot {
   bool torque = false;
   size_t rsz = 4;
   int n = 0;
+  size_t cap = 0;
 };
 
-constexpr int kSlots = 2;
+constexpr int kSlots = 4;
 constexpr size_t kLatencyWindow = 1 << 17;
 
 }  // namespace
@@ -115,7 +135,7 @@ struct fcm_server {
   std::unordered_map<long long, std::shared_ptr<Request>> table;
   // stats (under mu)
   long long submitted = 0, completed = 0, rejected = 0, canceled = 0, failed = 0;
-  long long batches = 0, batched_requests = 0, handles_created = 0, handles_evicted = 0;
+  long long batches = 0, batched_requests = 0, handles_created = 0, handles_evicted = 0, graph_passes = 0;
   std::vector<double> latency_us;   // ring of the latest completions
   size_t latency_next = 0;
   size_t hbm_bytes = 0;             // written by the worker, read under mu
@@ -124,6 +144,7 @@ struct fcm_server {
   Slot slots[kSlots];
   size_t used = 0;                  // handles + staging device bytes
   unsigned long long tick = 0;
+  cudaStream_t capture = nullptr;   // stream that graphs are captured on (nothing runs on it)
   std::thread worker;
   int init_status = FCM_OK;
   std::string init_error;
@@ -169,8 +190,9 @@ void finish_requests(fcm_server* s, std::vector<std::shared_ptr<Request>>& reqs,
   s->cv_done.notify_all();
 }
 
-int grow(Buffer* b, size_t bytes, bool host, size_t* used) {
+int grow(Buffer* b, size_t bytes, bool host, size_t* used, bool* moved) {
   if (b->bytes >= bytes) return FCM_OK;
+  *moved = true;
   const size_t want = pow2_at_least(bytes, 1 << 16);
   if (b->p) {
     if (host) cudaFreeHost(b->p);
@@ -190,7 +212,13 @@ int grow(Buffer* b, size_t bytes, bool host, size_t* used) {
 }
 
 void destroy_handle(fcm_server* s, std::list<CachedHandle>::iterator it) {
-  if (it->last) cudaEventDestroy(it->last);
+  for (auto& gr : it->graphs) cudaGraphExecDestroy(gr.second);
+  for (int k = 0; k < 2; ++k) {
+    if (it->d_in[k].p) cudaFree(it->d_in[k].p);
+    if (it->d_out[k].p) cudaFree(it->d_out[k].p);
+    if (it->set_free[k]) cudaEventDestroy(it->set_free[k]);
+  }
+  if (it->computed) cudaEventDestroy(it->computed);
   fcm_destroy(it->h);
   s->used -= it->bytes;
   s->cache.erase(it);
@@ -200,9 +228,8 @@ void destroy_handle(fcm_server* s, std::list<CachedHandle>::iterator it) {
 void complete_slot(fcm_server* s, Slot& sl, int status) {
   if (status == FCM_OK) {
     const size_t row = 3 * sl.rsz;
-    const size_t ntot = (size_t)sl.n;
     const char* U = static_cast<const char*>(sl.h_out.p);
-    const char* W = U + ntot * row;
+    const char* W = U + sl.cap * row;
     for (size_t k = 0; k < sl.reqs.size(); ++k) {
       Request& r = *sl.reqs[k];
       const size_t o = (size_t)sl.offsets[k] * row, bytes = (size_t)r.r.n * row;
@@ -243,7 +270,8 @@ bool any_busy(const fcm_server* s) {
 }
 
 // A cached handle for the class with room for (systems, n), creating one within the budget.
-int get_handle(fcm_server* s, const fcm_params& p, const std::string& key, int systems, int n, CachedHandle** out) {
+int get_handle(fcm_server* s, const fcm_params& p, const std::string& key, bool torque, int systems, int n,
+               CachedHandle** out) {
   *out = nullptr;
   for (auto it = s->cache.begin(); it != s->cache.end(); ++it) {
     if (it->key == key && it->max_systems >= systems && it->max_n >= n) {
@@ -257,7 +285,9 @@ int get_handle(fcm_server* s, const fcm_params& p, const std::string& key, int s
   q.max_n = (int)std::min<size_t>(pow2_at_least((size_t)n, 1024), (size_t)1 << 30);
   q.tile[0] = q.tile[1] = q.tile[2] = 0;
   q.spread_kernel = 0;
-  const size_t est = workspace_estimate(q, want_sys);
+  const size_t rsz = q.precision == FCM_FP64 ? sizeof(double) : sizeof(float);
+  const size_t stage_bytes = 2 * (size_t)q.max_n * 3 * rsz * ((torque ? 3 : 2) + 2);
+  const size_t est = workspace_estimate(q, want_sys) + stage_bytes;
   if (est > s->budget)
     return fail(FCM_ERR_OOM, "the request's workspace (" + std::to_string(est) + " bytes) exceeds the HBM budget (" +
                                  std::to_string(s->budget) + " bytes)");
@@ -284,13 +314,32 @@ int get_handle(fcm_server* s, const fcm_params& p, const std::string& key, int s
   ch.h = h;
   ch.max_systems = want_sys;
   ch.max_n = q.max_n;
-  ch.bytes = fcm_workspace_bytes(h);
+  ch.fp32 = q.precision == FCM_FP32;
+  ch.torque = torque;
+  ch.rsz = rsz;
   ch.last_use = ++s->tick;
-  if (cudaEventCreateWithFlags(&ch.last, cudaEventDisableTiming) != cudaSuccess) {
-    cudaGetLastError();
-    fcm_destroy(h);
-    return fail(FCM_ERR_CUDA, "event creation failed");
+  const size_t row = 3 * rsz;
+  cudaError_t ce = cudaEventCreateWithFlags(&ch.computed, cudaEventDisableTiming);
+  for (int k = 0; k < 2; ++k) {
+    ch.d_in[k].bytes = (size_t)q.max_n * row * (torque ? 3 : 2);
+    ch.d_out[k].bytes = (size_t)q.max_n * row * 2;
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&ch.set_free[k], cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaMalloc(&ch.d_in[k].p, ch.d_in[k].bytes);
+    if (ce == cudaSuccess) ce = cudaMalloc(&ch.d_out[k].p, ch.d_out[k].bytes);
   }
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    for (int k = 0; k < 2; ++k) {
+      if (ch.d_in[k].p) cudaFree(ch.d_in[k].p);
+      if (ch.d_out[k].p) cudaFree(ch.d_out[k].p);
+      if (ch.set_free[k]) cudaEventDestroy(ch.set_free[k]);
+    }
+    if (ch.computed) cudaEventDestroy(ch.computed);
+    fcm_destroy(h);
+    return fail(ce == cudaErrorMemoryAllocation ? FCM_ERR_OOM : FCM_ERR_CUDA,
+                std::string("handle staging: ") + cudaGetErrorString(ce));
+  }
+  ch.bytes = fcm_workspace_bytes(h) + 2 * (ch.d_in[0].bytes + ch.d_out[0].bytes);
   s->used += ch.bytes;
   s->cache.push_back(ch);
   {
@@ -321,7 +370,30 @@ std::vector<std::shared_ptr<Request>> take_batch(fcm_server* s) {
   return b;
 }
 
-// Stages a batch into a slot and enqueues its pass.
+// The captured pass of (handle, bucket, staging set), captured on first use.
+int graph_for(CachedHandle* ch, int bucket, int set, cudaStream_t stream, cudaGraphExec_t* out) {
+  *out = nullptr;
+  const auto key = std::make_pair(bucket, set);
+  auto it = ch->graphs.find(key);
+  if (it != ch->graphs.end()) {
+    *out = it->second;
+    return FCM_OK;
+  }
+  const size_t row = 3 * ch->rsz, cap = (size_t)ch->max_n;
+  char* din = static_cast<char*>(ch->d_in[set].p);
+  char* dout = static_cast<char*>(ch->d_out[set].p);
+  cudaGraphExec_t exec = nullptr;
+  int rc = capture_batch_graph(ch->h, bucket, din, din + cap * row, ch->torque ? din + 2 * cap * row : nullptr, dout,
+                               ch->torque ? dout + cap * row : nullptr, stream, &exec);
+  if (rc != FCM_OK) return rc;
+  ch->graphs[key] = exec;
+  *out = exec;
+  return FCM_OK;
+}
+
+// Stages a batch into a slot and enqueues its pass on the slot's stream, after the handle's
+// previous pass: inputs into the handle's staging, a replay of the captured pass for FP32 classes
+// (direct fcm_batch_apply otherwise, and if a capture ever failed), results back to the slot.
 int launch(fcm_server* s, Slot& sl, std::vector<std::shared_ptr<Request>>& reqs) {
   const Request& r0 = *reqs.front();
   sl.rsz = r0.rsz;
@@ -329,13 +401,14 @@ int launch(fcm_server* s, Slot& sl, std::vector<std::shared_ptr<Request>>& reqs)
   sl.offsets.assign(reqs.size() + 1, 0);
   for (size_t k = 0; k < reqs.size(); ++k) sl.offsets[k + 1] = sl.offsets[k] + reqs[k]->r.n;
   sl.n = sl.offsets.back();
-  const size_t row = 3 * sl.rsz, ntot = (size_t)sl.n;
-  const size_t in_bytes = (sl.torque ? 3 : 2) * ntot * row, out_bytes = 2 * ntot * row;
   CachedHandle* ch = nullptr;
-  int rc = get_handle(s, r0.r.params, r0.key, (int)reqs.size(), sl.n, &ch);
+  int rc = get_handle(s, r0.r.params, r0.key, r0.torque, (int)reqs.size(), sl.n, &ch);
   if (rc != FCM_OK) return rc;
-  if ((rc = grow(&sl.h_in, in_bytes, true, &s->used)) || (rc = grow(&sl.h_out, out_bytes, true, &s->used)) ||
-      (rc = grow(&sl.d_in, in_bytes, false, &s->used)) || (rc = grow(&sl.d_out, out_bytes, false, &s->used)))
+  const size_t row = 3 * sl.rsz, ntot = (size_t)sl.n;
+  sl.cap = (size_t)std::max(ch->max_n, 1);
+  const size_t in_bytes = (sl.torque ? 3 : 2) * sl.cap * row, out_bytes = 2 * sl.cap * row;
+  bool moved = false;
+  if ((rc = grow(&sl.h_in, in_bytes, true, &s->used, &moved)) || (rc = grow(&sl.h_out, out_bytes, true, &s->used, &moved)))
     return rc;
   char* hin = static_cast<char*>(sl.h_in.p);
   for (size_t k = 0; k < reqs.size(); ++k) {
@@ -343,42 +416,76 @@ int launch(fcm_server* s, Slot& sl, std::vector<std::shared_ptr<Request>>& reqs)
     const size_t o = (size_t)sl.offsets[k] * row, bytes = (size_t)q.n * row;
     if (bytes == 0) continue;
     std::memcpy(hin + o, q.pos, bytes);
-    std::memcpy(hin + ntot * row + o, q.F, bytes);
+    std::memcpy(hin + sl.cap * row + o, q.F, bytes);
     if (sl.torque) {
-      if (q.T) std::memcpy(hin + 2 * ntot * row + o, q.T, bytes);
-      else std::memset(hin + 2 * ntot * row + o, 0, bytes);
+      if (q.T) std::memcpy(hin + 2 * sl.cap * row + o, q.T, bytes);
+      else std::memset(hin + 2 * sl.cap * row + o, 0, bytes);
     }
   }
-  char* din = static_cast<char*>(sl.d_in.p);
-  char* dout = static_cast<char*>(sl.d_out.p);
+  const int set = ch->next_set;
+  ch->next_set ^= 1;
+  char* din = static_cast<char*>(ch->d_in[set].p);
+  char* dout = static_cast<char*>(ch->d_out[set].p);
   auto cuda = [&](cudaError_t e, const char* what) -> int {
     if (e == cudaSuccess) return FCM_OK;
     cudaGetLastError();
     return fail(FCM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
   };
-  if ((rc = cuda(cudaMemcpyAsync(din, hin, in_bytes, cudaMemcpyHostToDevice, sl.stream), "input copy"))) return rc;
-  if ((rc = cuda(cudaStreamWaitEvent(sl.stream, ch->last, 0), "handle ordering"))) return rc;
   const int nsys = (int)reqs.size();
-  if (ch->max_systems >= nsys) {
-    rc = fcm_batch_apply(ch->h, nsys, sl.offsets.data(), din, din + ntot * row, sl.torque ? din + 2 * ntot * row : nullptr,
-                         dout, sl.torque ? dout + ntot * row : nullptr, sl.stream);
-  } else {
-    rc = fail(FCM_ERR_ARG, "batch larger than the handle");
+  if (ch->max_systems < nsys) return fail(FCM_ERR_ARG, "batch larger than the handle");
+  // inputs into the staging set once its previous pass is done with it; kernels (and the offsets
+  // they read) once the handle's previous pass has computed
+  if ((rc = cuda(cudaStreamWaitEvent(sl.stream, ch->set_free[set], 0), "staging ordering"))) return rc;
+  for (int a = 0; a < (sl.torque ? 3 : 2); ++a) {
+    if ((rc = cuda(cudaMemcpyAsync(din + a * sl.cap * row, hin + a * sl.cap * row, ntot * row, cudaMemcpyHostToDevice,
+                                   sl.stream), "input copy")))
+      return rc;
   }
-  if (rc != FCM_OK) return rc;
-  if ((rc = cuda(cudaEventRecord(ch->last, sl.stream), "event"))) return rc;
-  if ((rc = cuda(cudaMemcpyAsync(sl.h_out.p, dout, out_bytes, cudaMemcpyDeviceToHost, sl.stream), "output copy")))
+  bool replayed = false;
+  if (ch->fp32 && ch->graphs_ok) {
+    int bucket = 1;
+    while (bucket < nsys) bucket <<= 1;
+    bucket = std::min(bucket, ch->max_systems);
+    for (int k = 0; k <= bucket; ++k) sl.h_off[k] = k <= nsys ? sl.offsets[k] : sl.n;
+    cudaGraphExec_t exec = nullptr;
+    if (graph_for(ch, bucket, set, s->capture, &exec) == FCM_OK) {
+      if ((rc = cuda(cudaStreamWaitEvent(sl.stream, ch->computed, 0), "handle ordering"))) return rc;
+      if ((rc = cuda(cudaMemcpyAsync(handle_sys_off(ch->h), sl.h_off, sizeof(int) * (size_t)(bucket + 1),
+                                     cudaMemcpyHostToDevice, sl.stream), "offsets copy")))
+        return rc;
+      if ((rc = cuda(cudaGraphLaunch(exec, sl.stream), "graph launch"))) return rc;
+      replayed = true;
+    } else {
+      ch->graphs_ok = false;   // capture is not available here: direct launches from now on
+    }
+  }
+  if (!replayed) {
+    if ((rc = cuda(cudaStreamWaitEvent(sl.stream, ch->computed, 0), "handle ordering"))) return rc;
+    rc = fcm_batch_apply(ch->h, nsys, sl.offsets.data(), din, din + sl.cap * row,
+                         sl.torque ? din + 2 * sl.cap * row : nullptr, dout, sl.torque ? dout + sl.cap * row : nullptr,
+                         sl.stream);
+    if (rc != FCM_OK) return rc;
+  }
+  if ((rc = cuda(cudaEventRecord(ch->computed, sl.stream), "event"))) return rc;
+  char* hout = static_cast<char*>(sl.h_out.p);
+  if ((rc = cuda(cudaMemcpyAsync(hout, dout, ntot * row, cudaMemcpyDeviceToHost, sl.stream), "output copy"))) return rc;
+  if (sl.torque &&
+      (rc = cuda(cudaMemcpyAsync(hout + sl.cap * row, dout + sl.cap * row, ntot * row, cudaMemcpyDeviceToHost, sl.stream),
+                 "output copy")))
     return rc;
+  if ((rc = cuda(cudaEventRecord(ch->set_free[set], sl.stream), "event"))) return rc;
   if ((rc = cuda(cudaEventRecord(sl.done, sl.stream), "event"))) return rc;
   ch->in_flight += 1;
   ch->last_use = ++s->tick;
   sl.ch = ch;
   sl.reqs = reqs;
   sl.busy = true;
+  (void)moved;
   {
     std::lock_guard<std::mutex> lock(s->mu);
     ++s->batches;
     s->batched_requests += (long long)reqs.size();
+    if (replayed) ++s->graph_passes;
     s->hbm_bytes = s->used;
   }
   return FCM_OK;
@@ -423,11 +530,11 @@ void worker_main(fcm_server* s) {
 void release_server(fcm_server* s) {
   cudaSetDevice(s->device);
   while (!s->cache.empty()) destroy_handle(s, s->cache.begin());
+  if (s->capture) cudaStreamDestroy(s->capture);
   for (Slot& sl : s->slots) {
     if (sl.h_in.p) cudaFreeHost(sl.h_in.p);
     if (sl.h_out.p) cudaFreeHost(sl.h_out.p);
-    if (sl.d_in.p) cudaFree(sl.d_in.p);
-    if (sl.d_out.p) cudaFree(sl.d_out.p);
+    if (sl.h_off) cudaFreeHost(sl.h_off);
     if (sl.done) cudaEventDestroy(sl.done);
     if (sl.stream) cudaStreamDestroy(sl.stream);
   }
@@ -459,10 +566,14 @@ int fcm_server_create(int device, size_t hbm_budget, int max_batch, fcm_server**
   s->max_batch = max_batch;
   s->latency_us.reserve(1024);
   cudaError_t e = cudaSuccess;
-  for (Slot& sl : s->slots) {
+  for (int k = 0; k < kSlots; ++k) {
+    Slot& sl = s->slots[k];
+    sl.index = k;
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&sl.h_off, sizeof(int) * (FCM_MAX_BATCH + 1));
   }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->capture, cudaStreamNonBlocking);
   cudaSetDevice(prev);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -558,6 +669,7 @@ int fcm_server_get_stats(fcm_server* s, fcm_server_stats* out) {
   out->batched_requests = s->batched_requests;
   out->handles_created = s->handles_created;
   out->handles_evicted = s->handles_evicted;
+  out->graph_passes = s->graph_passes;
   out->hbm_bytes = s->hbm_bytes;
   out->hbm_budget = s->budget;
   lat = s->latency_us;

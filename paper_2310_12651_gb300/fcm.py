@@ -60,7 +60,7 @@ class Request(ctypes.Structure):
 class ServerStats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_longlong) for name in
                 ("submitted", "completed", "rejected", "canceled", "failed", "pending", "batches", "batched_requests",
-                 "handles_created", "handles_evicted")] + [
+                 "handles_created", "handles_evicted", "graph_passes")] + [
         ("hbm_bytes", ctypes.c_size_t),
         ("hbm_budget", ctypes.c_size_t),
         ("latency_p50_us", ctypes.c_double),

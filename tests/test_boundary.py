@@ -106,7 +106,7 @@ def test_server_structs_match_header(fcm):
     assert _struct_fields("fcm_request") == [f[0] for f in fcm.Request._fields_]
     assert _struct_fields("fcm_server_stats") == [f[0] for f in fcm.ServerStats._fields_]
     assert ctypes.sizeof(fcm.Request) == 112 + 8 + 5 * 8
-    assert ctypes.sizeof(fcm.ServerStats) == 10 * 8 + 2 * 8 + 3 * 8
+    assert ctypes.sizeof(fcm.ServerStats) == 11 * 8 + 2 * 8 + 3 * 8
 
 
 @pytest.mark.parametrize("budget, max_batch, message", [(0, 4, "hbm_budget"), (1 << 30, 0, "max_batch"),

@@ -275,3 +275,21 @@ def test_symmetry_linearity_positivity_fp32(fcm):
     U3, W3 = run_gpu(s, fcm.FCM_FP32)
     assert_parity(U3, 2.0 * U1 - 3.0 * U2, 1e-5, "U linear")
     assert_parity(W3, 2.0 * W1 - 3.0 * W2, 1e-5, "W linear")
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_dilute_system_with_widened_pair_cells(fcm, precision):
+    """phi = 0.2%: an r_c cell would hold about one particle, so the library widens the pair cells
+    (side (8/rho)^(1/3) > r_c, five cells per side here); every pair within r_c must still be found."""
+    n, phi, M, Sigma = 1200, 0.002, 64, 2.5
+    L = inputs.box_edge(n, phi)
+    rc = op.cutoff_radius(Sigma, 1e-6, torques=True)
+    rho = n / L ** 3
+    assert (8.0 / rho) ** (1.0 / 3.0) > 1.3 * rc      # the widened side is what the kernels use
+    s = System(n, L, M, Sigma, op.support_points(Sigma, L / M, 4.8), rc, inputs.BASE_SEED + 71)
+    prec = fcm.FCM_FP32 if precision == "fp32" else fcm.FCM_FP64
+    tol = FP32_TOL if precision == "fp32" else FP64_TOL
+    U, W = run_gpu(s, prec, stages=fcm.STAGE_PAIR)
+    Uo, Wo = s.oracle(prec, stages=2)
+    assert_parity(U, Uo, tol, f"U pair stage, widened cells, {precision}")
+    assert_parity(W, Wo, tol, f"W pair stage, widened cells, {precision}")

@@ -1,5 +1,5 @@
 """The serving engine (fcm_server_*): continuous batching per grid class, HBM admission,
-bounded waits, cancellation.
+bounded waits, cancellation, passes replayed from captured CUDA graphs.
 
 The central check is "alone = in the mix": every request served in a mixed
 stream (several grid classes, uneven sizes, submitted from several threads so
@@ -60,6 +60,7 @@ def test_alone_equals_in_the_mix(fcm):
         st = srv.stats()
     assert st["completed"] == len(systems) and st["failed"] == 0 and st["rejected"] == 0
     assert st["batches"] < len(systems), st     # same-class requests shared passes
+    assert st["graph_passes"] == st["batches"], st   # every FP32 pass replayed a captured graph
     assert st["latency_p99_us"] >= st["latency_p50_us"] > 0
     for i, s in enumerate(systems):
         Ua, Wa = run_gpu(s, fcm.FCM_FP32)
@@ -108,6 +109,7 @@ def test_budget_evicts_idle_handles_and_rejects_oversize(fcm):
                 results.append((s, tk))
         st = srv.stats()
     assert st["rejected"] == 1 and st["hbm_bytes"] <= st["hbm_budget"]
+    assert st["graph_passes"] == st["batches"]        # graphs are re-captured after each eviction
     assert st["handles_evicted"] >= 4 and st["handles_created"] >= 6, st
     for s, tk in results[:2]:
         Ua, Wa = run_gpu(s, fcm.FCM_FP32)
