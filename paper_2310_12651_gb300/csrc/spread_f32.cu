@@ -4,7 +4,9 @@
 // B = dd/(2 Sigma^4), over each particle's M_G^3 window.
 //
 // spread_rows_kernel (default, M_G <= 16): every thread owns one (y, z) row of
-// the tile's extended region and keeps its EX x 3 sums in registers. All
+// the tile's extended region and keeps its EX x 3 sums in registers (for
+// M_G <= 14 a CTA takes two x-adjacent binning tiles, 16-point rows: a third
+// less halo per grid point). All
 // threads walk the tile's particles together; each particle's x/y/z profiles
 // are staged once in shared memory and read as broadcasts. No two threads add
 // to the same point, so there are no atomics and the order of the sum over
@@ -78,21 +80,49 @@ constexpr int rows_threads(int MGT) {
   return MGT <= 14 ? (((7 + MGT) * (7 + MGT) + 31) / 32) * 32 : kRowsMaxThreads;
 }
 
-template <int MGT, bool GUARD, bool TORQUE, bool SAMEW>
+// TX = 8: one binning tile per CTA. TX = 16: two x-adjacent binning tiles (8 points each) per CTA;
+// their particles are contiguous in the tile-sorted order (tiles are numbered x fastest), and the
+// wider rows add about a third less halo to the grid per grid point.
+template <int TX>
+__device__ inline bool spread_tile_range(const Geometry<float>& g, const int* __restrict__ tstart, int b, int* p0,
+                                         int* p1, TileOrigin* o, size_t* goff) {
+  if (TX == 8) {
+    *p0 = tstart[b];
+    *p1 = tstart[b + 1];
+    if (*p0 >= *p1) return false;
+    *o = tile_origin(g, local_tile(g, b, goff));
+    return true;
+  }
+  const int ntx = g.ntile[0], nsx = (ntx + 1) >> 1;
+  const int sper = nsx * g.ntile[1] * g.ntile[2];
+  const int sys = b / sper;
+  const int sl = b - sys * sper;
+  const int sx = sl % nsx, rest = sl / nsx;
+  const int t0 = sys * g.tiles_per + 2 * sx + ntx * rest;
+  const int t1 = t0 + ((2 * sx + 1 < ntx) ? 2 : 1);
+  *p0 = tstart[t0];
+  *p1 = tstart[t1];
+  if (*p0 >= *p1) return false;
+  *goff = (size_t)sys * (size_t)g.grid_stride;
+  o->ox0 = 2 * sx * g.tile[0];
+  o->oy0 = (rest % g.ntile[1]) * g.tile[1];
+  o->oz0 = (rest / g.ntile[1]) * g.tile[2];
+  return true;
+}
+
+template <int MGT, bool GUARD, bool TORQUE, bool SAMEW, int TX>
 __global__ void __launch_bounds__(rows_threads(MGT), 1) spread_rows_kernel(Geometry<float> g, KernelConsts<float> kc,
                                                                         const float4* __restrict__ pos,
                                                                         const float4* __restrict__ Fv,
                                                                         const float4* __restrict__ Tv,
                                                                         const int* __restrict__ tstart,
                                                                         float* __restrict__ grid) {
-  constexpr int TX = 8;
   constexpr int EXT = TX + MGT - 1;
   extern __shared__ float4 sm4[];
-  const int t = blockIdx.x;
-  const int p0 = tstart[t], p1 = tstart[t + 1];
-  if (p0 >= p1) return;
+  int p0, p1;
   size_t goff;
-  const TileOrigin o = tile_origin(g, local_tile(g, t, &goff));
+  TileOrigin o;
+  if (!spread_tile_range<TX>(g, tstart, blockIdx.x, &p0, &p1, &o, &goff)) return;
   grid += goff;
   const int MG = GUARD ? g.MG : MGT;
   const int EY = g.tile[1] + MG - 1, EZ = g.tile[2] + MG - 1;
@@ -127,7 +157,12 @@ __global__ void __launch_bounds__(rows_threads(MGT), 1) spread_rows_kernel(Geome
       (d == 0 ? tb.xt : (d == 1 ? tb.yt : tb.zt))[q * MGT + j] = v;
     }
     for (int q = threadIdx.x; q < np; q += blockDim.x) {
-      tb.po[q] = window_offset(g, o, window_starts(g, pos[base + q]));
+      int4 off = window_offset(g, o, window_starts(g, pos[base + q]));
+      if (TX != 8) {   // window start inside the (wider) row: recomputed without the 8-point clamp
+        const int3 i0 = window_starts(g, pos[base + q]);
+        off.x = min(max(wrap_once(i0.x, g.M[0]) - o.ox0, 0), TX - 1);
+      }
+      tb.po[q] = off;
       tb.pf[q] = Fv[base + q];
       tb.pt[q] = TORQUE ? Tv[base + q] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
@@ -165,7 +200,15 @@ __global__ void __launch_bounds__(rows_threads(MGT), 1) spread_rows_kernel(Geome
       switch (off.x) {
         FCM_ROW_CASE(0) FCM_ROW_CASE(1) FCM_ROW_CASE(2) FCM_ROW_CASE(3)
         FCM_ROW_CASE(4) FCM_ROW_CASE(5) FCM_ROW_CASE(6) FCM_ROW_CASE(7)
-        default: break;
+        default:
+          if (TX > 8) {
+            switch (off.x) {
+              FCM_ROW_CASE(8 % TX) FCM_ROW_CASE(9 % TX) FCM_ROW_CASE(10 % TX) FCM_ROW_CASE(11 % TX)
+              FCM_ROW_CASE(12 % TX) FCM_ROW_CASE(13 % TX) FCM_ROW_CASE(14 % TX) FCM_ROW_CASE(15 % TX)
+              default: break;
+            }
+          }
+          break;
       }
 #undef FCM_ROW_CASE
     }
@@ -320,15 +363,28 @@ size_t spread_smem_bytes(const int tile[3], int MG) {
   return tab > ext ? tab : ext;  // either kernel may be selected for this tile
 }
 
+// Row-stationary spread over pairs of x-adjacent binning tiles (16-point rows).
+constexpr bool kSpreadPairTiles = true;
+
 template <int MGT, bool GUARD, bool TORQUE, bool SAMEW>
 static void rows_variant(const Geometry<float>& g, const KernelConsts<float>& kc, const BinBuffers& b, float* grid,
                          cudaStream_t s) {
   const size_t smem = row_tables_bytes(MGT);
   const int threads = (((g.tile[1] + g.MG - 1) * (g.tile[2] + g.MG - 1) + 31) / 32) * 32;
-  auto k = spread_rows_kernel<MGT, GUARD, TORQUE, SAMEW>;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k<<<b.ntiles, threads, smem, s>>>(g, kc, (const float4*)b.t_pos, (const float4*)b.t_F, (const float4*)b.t_T,
-                                    b.tile_start, grid);
+  const float4* pos = (const float4*)b.t_pos;
+  const float4* F = (const float4*)b.t_F;
+  const float4* T = (const float4*)b.t_T;
+  if (kSpreadPairTiles && MGT <= 14) {   // two binning tiles per CTA (registers: 3 (16 + M_G - 1) sums)
+    const int nsys = g.nsys > 1 ? g.nsys : 1;
+    const int blocks = nsys * ((g.ntile[0] + 1) / 2) * g.ntile[1] * g.ntile[2];
+    auto k = spread_rows_kernel<MGT, GUARD, TORQUE, SAMEW, 16>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<blocks, threads, smem, s>>>(g, kc, pos, F, T, b.tile_start, grid);
+  } else {
+    auto k = spread_rows_kernel<MGT, GUARD, TORQUE, SAMEW, 8>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<b.ntiles, threads, smem, s>>>(g, kc, pos, F, T, b.tile_start, grid);
+  }
 }
 
 template <int MGT, bool GUARD, bool TORQUE, bool SAMEW>

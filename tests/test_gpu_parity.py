@@ -293,3 +293,20 @@ def test_dilute_system_with_widened_pair_cells(fcm, precision):
     Uo, Wo = s.oracle(prec, stages=2)
     assert_parity(U, Uo, tol, f"U pair stage, widened cells, {precision}")
     assert_parity(W, Wo, tol, f"W pair stage, widened cells, {precision}")
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_flat_box_like_the_applications(fcm, precision):
+    """A thin periodic slab on a 96 x 96 x 16 grid, the shape of the applications' 256^2 x 16 and
+    512^2 x 8 grids (Section 6): M_G close to M_z, cells and tiles wrap in z."""
+    prec = fcm.FCM_FP32 if precision == "fp32" else fcm.FCM_FP64
+    L = (72.0, 72.0, 12.0)
+    Sigma = 1.0
+    rc = op.cutoff_radius(Sigma, 1e-4, torques=True)
+    assert rc <= 6.0
+    s = System(900, L, (96, 96, 16), Sigma, 12, rc, inputs.BASE_SEED + 72)
+    U, W = run_gpu(s, prec)
+    Uo, Wo = s.oracle(prec)
+    tol = FP32_TOL if precision == "fp32" else FP64_TOL
+    assert_parity(U, Uo, tol, f"U flat slab {precision}")
+    assert_parity(W, Wo, tol, f"W flat slab {precision}")
