@@ -119,6 +119,36 @@ enum {
 int fcm_apply_stages(fcm_handle* h, int n, const void* pos, const void* F, const void* T,
                      void* U, void* W, int stages, void* stream);
 
+/* ---- Brownian increments (positive splitting) ------------------------------
+ * Section 3.3 shows that both M~ (grid part) and M - M~ (pairwise correction)
+ * are symmetric positive definite, which is what Brownian displacements need;
+ * Section 7 proposes fluctuating FCM for the grid part and a Lanczos square
+ * root for the pairwise part. fcm_brownian returns a velocity increment whose
+ * covariance over the random inputs is 2 kT (M~ + (M - M~)_VF):
+ *   grid part : u_B = sqrt(2 kT / h^3) G^{1/2} xi, G^{1/2} = F^-1 (I - k k^T/k^2)
+ *               / (sqrt(eta) |k|) F (k = 0 and Nyquist modes zero), interpolated
+ *               like the deterministic grid velocity (translation and rotation);
+ *   pair part : sqrt(2 kT) (M - M~)^{1/2} z for the force-velocity block (the
+ *               paper proves positive splitting for it; the torque blocks are
+ *               left out), by Lanczos iteration on the pair kernel.
+ *   kT    : thermal energy (> 0)
+ *   xi    : 3 M_x M_y M_z values (layout [c][z][y][x]), i.i.d. N(0, 1), or NULL
+ *           to leave out the grid part                             [device, read]
+ *   z     : (n, 3) i.i.d. N(0, 1), or NULL to leave out the pair part [device, read]
+ *   U     : (n, 3) translational increment velocity                [device, write]
+ *   W     : (n, 3) rotational (grid part only), or NULL            [device, write]
+ *   max_iter, tol : Lanczos limits (1 <= max_iter <= FCM_LANCZOS_MAX_ITER); it
+ *           stops when successive approximations differ by less than tol
+ *           (relative); *iterations receives the iterations used (may be NULL).
+ * Single-system use of any handle (system 0 of a batch handle). Synchronous:
+ * the Lanczos recurrence reads two scalars per iteration. Allocates its Lanczos
+ * basis ((max_iter + 1) x 3n values) on first use and keeps it until
+ * fcm_destroy. FCM_ERR_INPUT if the correction is not positive definite on the
+ * Krylov space. */
+#define FCM_LANCZOS_MAX_ITER 64
+int fcm_brownian(fcm_handle* h, int n, const void* pos, double kT, const void* xi, const void* z, void* U, void* W,
+                 int max_iter, double tol, int* iterations, void* stream);
+
 /* ---- Batched systems (many independent systems in one pass) ----------------
  * The paper treats one periodic system at a time; running many small systems
  * one call each leaves the GPU idle between launches. A batch handle holds up

@@ -225,6 +225,9 @@ struct fcm_handle {
   int max_systems = 1;
   int* sys_off = nullptr;       // device offsets of the current batched pass
   size_t spec_bytes = 0;        // one system's spectra
+  void* lz = nullptr;           // Lanczos basis and work vector (fcm_brownian), grown on demand
+  size_t lz_bytes = 0;
+  double* lz_dot = nullptr;     // device scalar of the Lanczos dot products
   size_t bytes = 0;
   long long launches = 0;
   std::vector<void*> allocs;
@@ -269,6 +272,8 @@ void release(fcm_handle* h) {
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->side) cudaStreamDestroy(h->side);
   for (void* p : h->allocs) cudaFree(p);
+  if (h->lz) cudaFree(h->lz);
+  if (h->lz_dot) cudaFree(h->lz_dot);
   delete h;
 }
 
@@ -675,7 +680,223 @@ size_t workspace_estimate(const fcm_params& p, int max_systems) {
 
 }  // namespace fcm
 
+namespace {
+
+// Eigen-decomposition of a small symmetric matrix (row-major n x n) by cyclic Jacobi rotations:
+// A = Q diag(w) Q^T. Used on the Lanczos tridiagonal matrix (n <= kLanczosMax).
+void jacobi_eig(std::vector<double> A, int n, std::vector<double>* w, std::vector<double>* Q) {
+  Q->assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) (*Q)[(size_t)i * n + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        const double v = A[(size_t)i * n + j] * A[(size_t)i * n + j];
+        tot += v;
+        if (i != j) off += v;
+      }
+    if (off <= 1e-30 * tot) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = A[(size_t)p * n + q];
+        if (apq == 0.0) continue;
+        const double theta = (A[(size_t)q * n + q] - A[(size_t)p * n + p]) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+        for (int k = 0; k < n; ++k) {   // columns p, q
+          const double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+          A[(size_t)k * n + p] = c * akp - sn * akq;
+          A[(size_t)k * n + q] = sn * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {   // rows p, q
+          const double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+          A[(size_t)p * n + k] = c * apk - sn * aqk;
+          A[(size_t)q * n + k] = sn * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double qkp = (*Q)[(size_t)k * n + p], qkq = (*Q)[(size_t)k * n + q];
+          (*Q)[(size_t)k * n + p] = c * qkp - sn * qkq;
+          (*Q)[(size_t)k * n + q] = sn * qkp + c * qkq;
+        }
+      }
+  }
+  w->resize(n);
+  for (int i = 0; i < n; ++i) (*w)[i] = A[(size_t)i * n + i];
+}
+
+static_assert(kLanczosMax == FCM_LANCZOS_MAX_ITER, "the Lanczos coefficient block holds every iteration");
+
+// Lanczos coefficients c = |z| T^{1/2} e_1 for the k x k tridiagonal T (diagonal alpha, off-diagonal
+// beta): the square root applied to z is then V c. False if T is not positive definite.
+bool lanczos_coef(const std::vector<double>& alpha, const std::vector<double>& beta, int k, double znorm,
+                  std::vector<double>* c) {
+  std::vector<double> T((size_t)k * k, 0.0), w, Q;
+  for (int i = 0; i < k; ++i) {
+    T[(size_t)i * k + i] = alpha[i];
+    if (i + 1 < k) T[(size_t)i * k + i + 1] = T[(size_t)(i + 1) * k + i] = beta[i];
+  }
+  jacobi_eig(T, k, &w, &Q);
+  c->assign(k, 0.0);
+  for (int j = 0; j < k; ++j) {
+    if (!(w[j] > 0.0)) return false;
+    const double s = std::sqrt(w[j]) * Q[(size_t)0 * k + j] * znorm;   // (Q^T e_1)_j = Q[0][j]
+    for (int i = 0; i < k; ++i) (*c)[i] += Q[(size_t)i * k + j] * s;
+  }
+  return true;
+}
+
+// Grid part: white grid noise xi -> u_B = sqrt(2 kT / h^3) G^{1/2} xi -> interpolated (U, W).
+template <typename R>
+int brownian_grid(fcm_handle* h, int n, const R* pos, const R* xi, double kT, R* U, R* W, cudaStream_t s) {
+  Geometry<R> g = *reinterpret_cast<const Geometry<R>*>(h->fp64 ? (const void*)&h->gd : (const void*)&h->gf);
+  g.nsys = 1;
+  BinBuffers bb = h->bb;
+  bb.nsys = 1;
+  bb.sys_off = nullptr;
+  bb.n_dev = nullptr;
+  bb.ntiles = g.tiles_per;
+  const fcm_handle::Plan* plan = plan_for(h, 1);
+  if (!plan) return fail(FCM_ERR_ARG, "no FFT plan for one system");
+  launch_binning<R>(g, n, pos, pos, nullptr, bb, false, s, &h->launches);   // tile order (forces unused)
+  FCM_CUDA(cudaMemcpyAsync(h->grid, xi, h->grid_bytes, cudaMemcpyDeviceToDevice, s));
+  const double h3 = (h->p.L[0] / h->p.M[0]) * (h->p.L[1] / h->p.M[1]) * (h->p.L[2] / h->p.M[2]);
+  const R factor = (R)std::sqrt(2.0 * kT / h3);
+  FCM_CUFFT(cufftSetStream(plan->r2c, s));
+  FCM_CUFFT(cufftSetStream(plan->c2r, s));
+  if constexpr (std::is_same<R, double>::value) {
+    FCM_CUFFT(cufftExecD2Z(plan->r2c, (cufftDoubleReal*)h->grid, (cufftDoubleComplex*)h->spec));
+    launch_projection_sqrt<double>(g, h->p.eta, factor, h->spec, s, &h->launches);
+    FCM_CUFFT(cufftExecZ2D(plan->c2r, (cufftDoubleComplex*)h->spec, (cufftDoubleReal*)h->grid));
+    launch_gather_f64(g, h->kd, W != nullptr, bb, n, (const double*)h->grid, nullptr, nullptr, U, W, s, &h->launches);
+  } else {
+    FCM_CUFFT(cufftExecR2C(plan->r2c, (cufftReal*)h->grid, (cufftComplex*)h->spec));
+    launch_projection_sqrt<float>(g, (float)h->p.eta, factor, h->spec, s, &h->launches);
+    FCM_CUFFT(cufftExecC2R(plan->c2r, (cufftComplex*)h->spec, (cufftReal*)h->grid));
+    launch_gather_f32(g, h->kf, W != nullptr, bb, (const float*)h->grid, nullptr, nullptr, U, W, s, &h->launches);
+  }
+  FCM_CUDA(cudaGetLastError());
+  return FCM_OK;
+}
+
+int read_dot(fcm_handle* h, cudaStream_t s, double* v) {
+  FCM_CUDA(cudaMemcpyAsync(v, h->lz_dot, sizeof(double), cudaMemcpyDeviceToHost, s));
+  FCM_CUDA(cudaStreamSynchronize(s));
+  return FCM_OK;
+}
+
+// Pair part: U += sqrt(2 kT) (M - M~)^{1/2} z by Lanczos (Krylov basis V, tridiagonal T), the
+// matrix-vector product being the pair stage applied to forces.
+template <typename R>
+int brownian_pair(fcm_handle* h, int n, const R* pos, const R* z, double kT, R* U, int max_iter, double tol,
+                  int* iterations, cudaStream_t s) {
+  const size_t m = 3 * (size_t)n;
+  const size_t need = sizeof(R) * m * (size_t)(max_iter + 1);
+  if (h->lz_bytes < need) {
+    if (h->lz) cudaFree(h->lz);
+    h->lz = nullptr;
+    h->lz_bytes = 0;
+    cudaError_t e = cudaMalloc(&h->lz, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(FCM_ERR_OOM, "Lanczos workspace of " + std::to_string(need) + " bytes: " + cudaGetErrorString(e));
+    }
+    h->lz_bytes = need;
+  }
+  if (!h->lz_dot) FCM_CUDA(cudaMalloc((void**)&h->lz_dot, sizeof(double)));
+  R* V = (R*)h->lz;
+  R* w = V + m * (size_t)max_iter;
+  int rc;
+  double zz = 0.0;
+  launch_dot<R>(z, z, m, h->lz_dot, s, &h->launches);
+  if ((rc = read_dot(h, s, &zz))) return rc;
+  *iterations = 0;
+  if (!(zz > 0.0)) return FCM_OK;
+  const double znorm = std::sqrt(zz);
+  launch_axpby<R>(V, 1.0 / znorm, z, 0.0, m, s, &h->launches);
+  std::vector<double> alpha, beta, c, cprev;
+  int k = 0;
+  for (int j = 0; j < max_iter; ++j) {
+    R* vj = V + m * (size_t)j;
+    if ((rc = run<R>(h, 1, n, pos, vj, nullptr, w, nullptr, FCM_STAGE_PAIR, false, s))) return rc;
+    if (j > 0) launch_axpby<R>(w, -beta[j - 1], V + m * (size_t)(j - 1), 1.0, m, s, &h->launches);
+    double a = 0.0, bb2 = 0.0;
+    launch_dot<R>(w, vj, m, h->lz_dot, s, &h->launches);
+    if ((rc = read_dot(h, s, &a))) return rc;
+    launch_axpby<R>(w, -a, vj, 1.0, m, s, &h->launches);
+    launch_dot<R>(w, w, m, h->lz_dot, s, &h->launches);
+    if ((rc = read_dot(h, s, &bb2))) return rc;
+    alpha.push_back(a);
+    k = j + 1;
+    if (!lanczos_coef(alpha, beta, k, znorm, &c))
+      return fail(FCM_ERR_INPUT, "the pairwise correction is not positive definite on this Krylov space");
+    double diff = 0.0, cn = 0.0;
+    for (int i = 0; i < k; ++i) {
+      const double d = c[i] - (i < (int)cprev.size() ? cprev[i] : 0.0);
+      diff += d * d;
+      cn += c[i] * c[i];
+    }
+    cprev = c;
+    const double b = std::sqrt(std::max(bb2, 0.0));
+    if ((j > 0 && diff <= tol * tol * cn) || b <= 1e-14 * std::fabs(a) || j + 1 == max_iter) break;
+    beta.push_back(b);
+    launch_axpby<R>(V + m * (size_t)(j + 1), 1.0 / b, w, 0.0, m, s, &h->launches);
+  }
+  LanczosCoef lc{};
+  const double amp = std::sqrt(2.0 * kT);
+  for (int i = 0; i < k; ++i) lc.c[i] = amp * c[i];
+  launch_combine<R>(U, V, lc, k, m, true, s, &h->launches);
+  FCM_CUDA(cudaGetLastError());
+  *iterations = k;
+  return FCM_OK;
+}
+
+template <typename R>
+int brownian(fcm_handle* h, int n, const R* pos, double kT, const R* xi, const R* z, R* U, R* W, int max_iter,
+             double tol, int* iterations, cudaStream_t s) {
+  int rc;
+  if (xi) {
+    if ((rc = brownian_grid<R>(h, n, pos, xi, kT, U, W, s))) return rc;
+  } else {
+    launch_zero(U, sizeof(R) * 3 * (size_t)n, s, &h->launches);
+    if (W) launch_zero(W, sizeof(R) * 3 * (size_t)n, s, &h->launches);
+  }
+  int it = 0;
+  if (z && h->pairs_on) {
+    if ((rc = brownian_pair<R>(h, n, pos, z, kT, U, max_iter, tol, &it, s))) return rc;
+  }
+  if (iterations) *iterations = it;
+  FCM_CUDA(cudaStreamSynchronize(s));
+  return FCM_OK;
+}
+
+}  // namespace
+
 #pragma GCC visibility push(default)
+extern "C" {
+
+int fcm_brownian(fcm_handle* h, int n, const void* pos, double kT, const void* xi, const void* z, void* U, void* W,
+                 int max_iter, double tol, int* iterations, void* stream) {
+  if (iterations) *iterations = 0;
+  if (!h) return fail(FCM_ERR_ARG, "handle is NULL");
+  if (n < 0 || n > h->p.max_n)
+    return fail(FCM_ERR_ARG, "n = " + std::to_string(n) + " outside [0, max_n = " + std::to_string(h->p.max_n) + "]");
+  if (!(kT > 0.0) || !std::isfinite(kT)) return fail(FCM_ERR_ARG, "kT must be finite and > 0");
+  if (max_iter < 1 || max_iter > FCM_LANCZOS_MAX_ITER)
+    return fail(FCM_ERR_ARG, "max_iter must be in [1, " + std::to_string(FCM_LANCZOS_MAX_ITER) + "]");
+  if (!(tol > 0.0)) return fail(FCM_ERR_ARG, "tol must be > 0");
+  if (n > 0 && (!pos || !U)) return fail(FCM_ERR_ARG, "pos and U must be non-NULL when n > 0");
+  if (n == 0) return FCM_OK;
+  DeviceGuard guard(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (h->fp64)
+    return brownian<double>(h, n, (const double*)pos, kT, (const double*)xi, (const double*)z, (double*)U,
+                            (double*)W, max_iter, tol, iterations, s);
+  return brownian<float>(h, n, (const float*)pos, kT, (const float*)xi, (const float*)z, (float*)U, (float*)W,
+                         max_iter, tol, iterations, s);
+}
+
+}  // extern "C"
+
 extern "C" {
 
 int fcm_version(void) { return 10000; }

@@ -284,6 +284,21 @@ void launch_binning(const Geometry<R>& g, int n, const R* pos, const R* F, const
 
 template <typename R>
 void launch_projection(const Geometry<R>& g, R eta, void* spectrum, cudaStream_t s, long long* launches);
+// factor (I - k k^T/k^2) / (sqrt(eta) |k| M) in place, same zero modes (one system).
+template <typename R>
+void launch_projection_sqrt(const Geometry<R>& g, R eta, R factor, void* spectrum, cudaStream_t s,
+                            long long* launches);
+
+// Vector kernels of the Lanczos iteration (length m, FP64 accumulation of dot products).
+constexpr int kLanczosMax = 64;
+struct LanczosCoef { double c[kLanczosMax]; };
+template <typename R>
+void launch_dot(const R* a, const R* b, size_t m, double* out, cudaStream_t s, long long* launches);
+template <typename R>   // y = alpha x + beta y
+void launch_axpby(R* y, double alpha, const R* x, double beta, size_t m, cudaStream_t s, long long* launches);
+template <typename R>   // out = sum_j c_j V[j] (+ out when accumulate), V[j] = V + j m
+void launch_combine(R* out, const R* V, const LanczosCoef& c, int k, size_t m, bool accumulate, cudaStream_t s,
+                    long long* launches);
 
 // FP32 tiled spread / gather (tile accumulation, halo flush).
 size_t tile_smem_bytes(const int tile[3], int MG);      // extended region (gather, atomic spread)

@@ -4,8 +4,11 @@
 // M_x/2 + 1) of each system of a launch (blockIdx.y). The factor 1/M of the
 // unnormalised inverse FFT is folded in. The k = 0 mode and every mode with an
 // index on a Nyquist plane (M_i/2 of an even M_i) are set to zero. One thread
-// per complex mode, 3 x 2 loads and stores.
+// per complex mode, 3 x 2 loads and stores. The square-root variant, with the
+// same zero modes, turns white grid noise into a velocity field whose covariance
+// is the operator itself (Brownian increments).
 #include <cuComplex.h>
+#include <cmath>
 #include "fcm_internal.cuh"
 
 namespace fcm {
@@ -20,7 +23,9 @@ __device__ inline R wavenumber(int i, int M, R twopi_over_L) {
   return R(s) * twopi_over_L;
 }
 
-template <typename R>
+// SQRT: the square root of the operator instead, (I - k k^T / k^2) / |k| (the projector is
+// idempotent), for grid noise in Brownian increments.
+template <typename R, bool SQRT>
 __global__ void __launch_bounds__(256) project_kernel(Geometry<R> g, R scale, typename Cplx<R>::T* spec,
                                                       size_t ncplx) {
   typedef typename Cplx<R>::T C2;
@@ -51,7 +56,7 @@ __global__ void __launch_bounds__(256) project_kernel(Geometry<R> g, R scale, ty
   R ik2 = R(1) / k2;
   R dre = (kx * a.x + ky * b.x + kz * c.x) * ik2;
   R dim = (kx * a.y + ky * b.y + kz * c.y) * ik2;
-  R sc = scale * ik2;
+  R sc = SQRT ? scale / sqrt(k2) : scale * ik2;
   a.x = (a.x - kx * dre) * sc; a.y = (a.y - kx * dim) * sc;
   b.x = (b.x - ky * dre) * sc; b.y = (b.y - ky * dim) * sc;
   c.x = (c.x - kz * dre) * sc; c.y = (c.y - kz * dim) * sc;
@@ -65,9 +70,24 @@ void launch_projection(const Geometry<R>& g, R eta, void* spectrum, cudaStream_t
   R scale = R(1.0 / ((double)eta * mtot));
   unsigned blocks = (unsigned)((ncplx + 255) / 256);
   const unsigned nsys = g.nsys > 1 ? (unsigned)g.nsys : 1u;
-  project_kernel<R><<<dim3(blocks, nsys), 256, 0, s>>>(g, scale, (typename Cplx<R>::T*)spectrum, ncplx);
+  project_kernel<R, false><<<dim3(blocks, nsys), 256, 0, s>>>(g, scale, (typename Cplx<R>::T*)spectrum, ncplx);
   *launches += 1;
 }
+
+template <typename R>
+void launch_projection_sqrt(const Geometry<R>& g, R eta, R factor, void* spectrum, cudaStream_t s,
+                            long long* launches) {
+  size_t ncplx = (size_t)(g.M[0] / 2 + 1) * g.M[1] * g.M[2];
+  double mtot = (double)g.M[0] * g.M[1] * g.M[2];
+  R scale = R((double)factor / (std::sqrt((double)eta) * mtot));
+  unsigned blocks = (unsigned)((ncplx + 255) / 256);
+  project_kernel<R, true><<<dim3(blocks, 1), 256, 0, s>>>(g, scale, (typename Cplx<R>::T*)spectrum, ncplx);
+  *launches += 1;
+}
+
+template void launch_projection_sqrt<float>(const Geometry<float>&, float, float, void*, cudaStream_t, long long*);
+template void launch_projection_sqrt<double>(const Geometry<double>&, double, double, void*, cudaStream_t,
+                                             long long*);
 
 template void launch_projection<float>(const Geometry<float>&, float, void*, cudaStream_t, long long*);
 template void launch_projection<double>(const Geometry<double>&, double, void*, cudaStream_t, long long*);

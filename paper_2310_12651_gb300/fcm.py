@@ -82,6 +82,7 @@ def _load():
         "fcm_batch_apply": (i, [vp, i, ctypes.POINTER(i), vp, vp, vp, vp, vp, vp]),
         "fcm_batch_apply_stages": (i, [vp, i, ctypes.POINTER(i), vp, vp, vp, vp, vp, i, vp]),
         "fcm_max_systems": (i, [vp]),
+        "fcm_brownian": (i, [vp, i, vp, d, vp, vp, vp, vp, i, d, ctypes.POINTER(i), vp]),
         "fcm_destroy": (i, [vp]),
         "fcm_apply": (i, [vp, i, vp, vp, vp, vp, vp, vp]),
         "fcm_apply_stages": (i, [vp, i, vp, vp, vp, vp, vp, i, vp]),
@@ -114,13 +115,16 @@ _lib = _load()
 
 #: symbols declared in include/fcm.h, for the export check
 EXPORTED = ("fcm_version", "fcm_params_default", "fcm_create", "fcm_destroy", "fcm_apply", "fcm_apply_stages",
-            "fcm_create_batch", "fcm_batch_apply", "fcm_batch_apply_stages", "fcm_max_systems", "fcm_spread", "fcm_copy_grid", "fcm_check", "fcm_set_timing", "fcm_read_timing", "fcm_launch_count",
+            "fcm_create_batch", "fcm_batch_apply", "fcm_batch_apply_stages", "fcm_max_systems", "fcm_brownian",
+            "fcm_spread", "fcm_copy_grid", "fcm_check", "fcm_set_timing", "fcm_read_timing", "fcm_launch_count",
             "fcm_workspace_bytes", "fcm_cutoff_radius", "fcm_pair_correction_noalloc", "fcm_last_error",
             "fcm_server_create", "fcm_server_submit", "fcm_server_poll", "fcm_server_cancel", "fcm_server_get_stats",
             "fcm_server_reset_latency", "fcm_server_destroy")
 
 #: most systems of one batched pass (include/fcm.h)
 MAX_BATCH = 1024
+#: most Lanczos iterations of fcm_brownian (include/fcm.h)
+LANCZOS_MAX_ITER = 64
 
 #: capacity of fcm_pair_correction_noalloc's fixed scratch (include/fcm.h)
 NOALLOC_MAX_N = 65536
@@ -215,6 +219,13 @@ class Handle:
         arr = (ctypes.c_int * max(len(offsets), 1))(*[int(v) for v in offsets])
         _check(_lib.fcm_batch_apply_stages(self._h, int(n_sys), arr, _ptr(pos), _ptr(F), _ptr(T), _ptr(U), _ptr(W),
                                            int(stages), stream or None))
+
+    def brownian(self, n, pos, kT, xi, z, U, W=None, max_iter=40, tol=1e-6, stream=0) -> int:
+        """Brownian increment velocity (positive splitting); returns the Lanczos iterations used."""
+        it = ctypes.c_int()
+        _check(_lib.fcm_brownian(self._h, int(n), _ptr(pos), float(kT), _ptr(xi), _ptr(z), _ptr(U), _ptr(W),
+                                 int(max_iter), float(tol), ctypes.byref(it), stream or None))
+        return it.value
 
     def spread(self, n, pos, F, T, stream=0):
         _check(_lib.fcm_spread(self._h, int(n), _ptr(pos), _ptr(F), _ptr(T), stream or None))
