@@ -51,7 +51,7 @@ WORKLOADS = {
 }
 # dram__bytes_read.sum + dram__bytes_write.sum per system of a launch (cold caches), from one ncu capture of
 # the current kernels; a launch over B systems moves B times this. None once a kernel changes after the capture.
-TRAFFIC_BYTES = {"c2": {"spread": 28.78e6, "gather": 26.59e6, "pair": 3.18e6}}
+TRAFFIC_BYTES = {"c2": {"spread": None, "gather": 26.59e6, "pair": 3.18e6}}
 
 
 def workload(name="c2", n=None, h_ref=None):
@@ -357,6 +357,39 @@ def crossover_study(device, a_over_L=(0.012, 0.008), tols=(1e-4, 1e-6),
     return {"rows": rows, "crossings": crossings}
 
 
+def brownian_bench(device, reps=5, tol=1e-6):
+    """fcm_brownian on one system of the 128^3 workload (N = 65,536, phi = 5%, Sigma = 2a, FP32): the
+    grid part (noise -> square-root Stokes projection -> interpolation) and the Lanczos pair part,
+    each timed on its own (the call is synchronous; host wall clock around the call)."""
+    import numpy as np
+    import torch
+    from paper_2310_12651_gb300 import fcm, inputs
+    w = workload("c2")
+    n, M = w["n"], w["M"]
+    dev = torch.device("cuda", device)
+    Y = inputs.random_suspension(n, w["L"], inputs.BASE_SEED + 1)
+    rng = np.random.default_rng(2310127400)
+    pos = torch.as_tensor(Y, dtype=torch.float32, device=dev)
+    xi = torch.as_tensor(rng.standard_normal(3 * M ** 3), dtype=torch.float32, device=dev)
+    z = torch.as_tensor(rng.standard_normal((n, 3)), dtype=torch.float32, device=dev)
+    U = torch.empty_like(pos)
+    W = torch.empty_like(pos)
+    st = torch.cuda.current_stream(dev).cuda_stream
+    out = {}
+    with fcm.Handle(fcm.make_params(w["L"], M, w["Sigma"], w["r_c"], w["M_G"], n, fcm.FCM_FP32), device) as h:
+        for name, (a, b, ww) in {"grid_part": (xi, None, W), "pair_part": (None, z, None)}.items():
+            h.brownian(n, pos, 1.0, a, b, U, ww, max_iter=40, tol=tol, stream=st)
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                it = h.brownian(n, pos, 1.0, a, b, U, ww, max_iter=40, tol=tol, stream=st)
+            ms = (time.perf_counter() - t0) * 1e3 / reps
+            out[name] = {"ms": ms, "lanczos_iterations": it}
+    out["workload"] = (f"one system of N={n}, phi=5%, {M}^3, Sigma=2a, M_G={w['M_G']}, r_c={w['r_c']:.2f}a, FP32, "
+                       f"Lanczos tol {tol:g}; synchronous call timed on the host")
+    out["particle_increments_per_s"] = n / ((out["grid_part"]["ms"] + out["pair_part"]["ms"]) * 1e-3)
+    return out
+
+
 SERVE_CLASSES = 8          # box-size ladder of the serving mix (log-spaced L, one grid class each)
 SERVE_POOL = 32            # distinct systems drawn for the mix (half spheres, half 64-sphere rods)
 
@@ -513,6 +546,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-mix measurement")
     ap.add_argument("--no-sweep", action="store_true", help="skip the paper-settings PTPS sweep")
     ap.add_argument("--no-rods", action="store_true", help="skip the filament-layout measurement")
+    ap.add_argument("--no-brownian", action="store_true", help="skip the Brownian-increment measurement")
     ap.add_argument("--sweep-full", action="store_true", help="include the 12.8%% (N = 1.96M) sweep row")
     ap.add_argument("--serve-requests", type=int, default=1024)
     ap.add_argument("--mode", default="batched", choices=["batched", "single"],
@@ -692,6 +726,7 @@ def main():
         serve = serve_bench(local, requests=args.serve_requests)
     sweep = None if args.no_sweep else paper_sweep(local, full=args.sweep_full)
     rods = None if args.no_rods else rods_bench(local)
+    brown = None if args.no_brownian else brownian_bench(local)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -708,7 +743,7 @@ def main():
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B * 3 * n * 3 * 4,
                    "d2h_bytes_per_step": B * 2 * n * 3 * 4},
            "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
-           "fp64_plain": fp64, "serve": serve, "paper_sweep": sweep, "rods": rods,
+           "fp64_plain": fp64, "serve": serve, "paper_sweep": sweep, "rods": rods, "brownian": brown,
            "speedup_vs_fp64_plain": (value / world / fp64["value"]) if fp64 else None,
            "stages": stages_out, "step_ms_median": statistics.median(step_ms),
            "workspace_bytes": h.workspace_bytes()}
