@@ -22,6 +22,14 @@ grid_fcm
 params
     Window rule, cutoff-radius rule and grid-support rule used by both the
     standard and the fast oracle.
+brownian
+    Brownian increments by positive splitting (Section 3.3): grid noise through
+    the square root of the Stokes operator, and the exact square root of the
+    pairwise correction.
+rigid
+    Mobility problem of rigid bodies made of FCM particles (Section 6.1): the
+    saddle-point system solved densely, and Broyden's method started from the
+    diagonal-mobility Jacobian.
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test against
 a route that does not go through this package (Fourier quadrature, closed-form

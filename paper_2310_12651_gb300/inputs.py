@@ -170,3 +170,59 @@ def random_loads(n: int, seed: int, torques: bool = True, mean_free: bool = True
     if bias is not None:
         F = F + np.asarray(bias, dtype=np.float64)[None, :]
     return F, T
+
+
+#: FCM particles per rod and the doublet layout of the sedimenting-rod suspensions (Section 6.1)
+ROD_DOUBLETS = 11
+ROD_PITCH = math.sqrt(2.0)   # axial distance between consecutive doublets, in units of a
+
+
+def doublet_rods(n_rods: int, L_xy: float, L_z: float, seed: int, doublets: int = ROD_DOUBLETS,
+                 a: float = 1.0, lattice: bool = True) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """Planar rods built from alternating doublets of FCM particles (Section 6.1).
+
+    A rod has ``doublets`` doublets spaced ``ROD_PITCH * a`` along its axis; the two
+    particles of a doublet sit at +-a from the axis, alternately along the in-plane
+    normal and along z, so neighbouring particles are 2a apart and 11 doublets give
+    the rod length 10 sqrt(2) a = 14.14a. Rod centres lie in the plane z = L_z/2 on a
+    square lattice (``lattice``) or uniformly at random, axes in the plane at a random
+    angle. Returns (positions wrapped into the box (n_rods * 2 * doublets, 3),
+    body offsets (n_rods + 1,) int32, rod centres (n_rods, 3)); the particles of rod b
+    are rows body_off[b] .. body_off[b+1]-1 and rod b's centre is their centroid.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    per = 2 * doublets
+    if lattice:
+        side = int(math.ceil(math.sqrt(n_rods)))
+        spacing = L_xy / side
+        k = np.arange(n_rods)
+        cx = (k % side + 0.5) * spacing
+        cy = (k // side + 0.5) * spacing
+    else:
+        cx = rng.random(n_rods) * L_xy
+        cy = rng.random(n_rods) * L_xy
+    centres = np.stack([cx, cy, np.full(n_rods, 0.5 * L_z)], axis=1)
+    th = rng.uniform(0.0, 2.0 * math.pi, n_rods)
+    axis = np.stack([np.cos(th), np.sin(th), np.zeros(n_rods)], axis=1)
+    normal = np.stack([-np.sin(th), np.cos(th), np.zeros(n_rods)], axis=1)
+    ez = np.array([0.0, 0.0, 1.0])
+    off = np.empty((n_rods, per, 3))
+    for d in range(doublets):
+        s = (d - 0.5 * (doublets - 1)) * ROD_PITCH * a
+        lat = normal if d % 2 == 0 else np.broadcast_to(ez, (n_rods, 3))
+        off[:, 2 * d] = s * axis + a * lat
+        off[:, 2 * d + 1] = s * axis - a * lat
+    box = np.array([L_xy, L_xy, L_z])
+    pos = np.mod(centres[:, None, :] + off, box).reshape(-1, 3)
+    pos = np.minimum(pos, np.nextafter(box, 0))
+    body_off = (np.arange(n_rods + 1) * per).astype(np.int32)
+    return pos, body_off, centres
+
+
+def rod_loads(n_rods: int, seed: int, gravity=(1.0, 0.0, 0.0), per_rod: int = 2 * ROD_DOUBLETS,
+              scale: float = 0.0) -> np.ndarray:
+    """Rod forces and torques (n_rods, 6): per_rod * gravity plus i.i.d. N(0, scale^2) parts."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ft = rng.normal(size=(n_rods, 6)) * scale
+    ft[:, :3] += per_rod * np.asarray(gravity, dtype=np.float64)[None, :]
+    return ft

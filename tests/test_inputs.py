@@ -72,3 +72,22 @@ def test_serving_pool_shares_parameters_within_a_class():
         assert s["params"].M[0] == ch["M"] and 32 <= ch["M"] <= 256
         assert s["n"] * 4 * np.pi / 3 / L ** 3 <= 0.2 + 1e-9
         assert all(a.dtype == np.float32 and a.shape == (s["n"], 3) for a in s["arrays"])
+
+
+def test_doublet_rods_geometry():
+    """Rods of 11 alternating doublets: neighbours 2a apart, length 10 sqrt(2) a = 14.14a,
+    centroid at the rod centre in the plane z = L_z/2, lattice spacing L/ceil(sqrt(N_R))."""
+    from scipy.spatial.distance import pdist
+    pos, off, X = inputs.doublet_rods(9, 60.0, 24.0, inputs.BASE_SEED + 300)
+    assert pos.shape == (9 * 22, 3) and off.tolist() == list(range(0, 9 * 22 + 1, 22))
+    assert np.allclose(X[:, 2], 12.0) and np.allclose(sorted(set(np.round(X[:, 0], 9))), [10.0, 30.0, 50.0])
+    for b in range(9):
+        r = pos[off[b]:off[b + 1]] - X[b]
+        r -= np.array([60.0, 60.0, 24.0]) * np.round(r / np.array([60.0, 60.0, 24.0]))
+        assert np.allclose(r.mean(axis=0), 0.0, atol=1e-12)
+        assert abs(pdist(r).min() - 2.0) < 1e-12
+        ends = 0.5 * (r[20] + r[21]) - 0.5 * (r[0] + r[1])
+        assert abs(np.linalg.norm(ends) - 10 * np.sqrt(2.0)) < 1e-12 and abs(ends[2]) < 1e-12
+        assert np.allclose(np.sort(r[:, 2]), np.sort(-r[:, 2]))   # symmetric about the plane
+    ft = inputs.rod_loads(5, 1, gravity=(1.0, 0.0, 0.0))
+    assert np.allclose(ft, [[22.0, 0, 0, 0, 0, 0]] * 5)
