@@ -390,6 +390,122 @@ def brownian_bench(device, reps=5, tol=1e-6):
     return out
 
 
+def rod_suspension_params(L_xy, L_z, n, tol, precision=None):
+    """Fast-FCM parameters for the planar rod suspensions of Section 6.1 (box L_xy x L_xy x L_z, rods
+    in the plane z = L_z/2, forces only): for grid spacings h on a ladder, Sigma = (Table 1 ratio) h,
+    M_G from the window rule and r_c from the neighbour-aware cutoff with the in-plane density
+    (n / L_xy^2 particles per area: about 0.75 n / (L_xy^2 r_c) per volume within r_c of a particle);
+    r_c must stay below L_z / 2. Keeps the admissible spacing of least modelled cost."""
+    from paper_2310_12651_gb300 import fcm, tune
+    ratio = tune.resolution_for(tune.GRID_SHARE * tol)
+    c = tune.truncation_for(tune.GRID_SHARE * tol)
+    best = None
+    for h in (3.0, 3.5, 4.0, 4.5, 5.0, 5.5, 6.0):
+        Mxy = tune.grid_for(L_xy, h, 1.0)
+        Mz = tune.grid_for(L_z, h, 1.0)
+        hmax = max(L_xy / Mxy, L_z / Mz)
+        Sigma = ratio * hmax
+        MG = tune.support_points(Sigma, min(L_xy / Mxy, L_z / Mz), c)
+        if MG > 24 or MG > Mz:
+            continue
+        rc = tune.cutoff(Sigma, 0.5 * tol, torques=False)
+        for _ in range(3):
+            rc = tune.pair_cutoff(Sigma, tol, 0.75 * n / (L_xy ** 2 * rc), torques=False)
+        if rc > 0.5 * L_z:
+            continue
+        cand = n / L_xy ** 2 * math.pi * (1.5 * rc) ** 2
+        cost = (tune.COST["point"] * n * MG ** 3 + tune.COST["candidate"] * n * cand
+                + tune.COST["grid"] * Mxy * Mxy * Mz)
+        if best is None or cost < best["cost_model_s"]:
+            best = dict(M=(Mxy, Mxy, Mz), Sigma=Sigma, M_G=MG, r_c=rc, h=hmax, cost_model_s=cost)
+    if best is None:
+        raise ValueError("no admissible parameters for the rod suspension")
+    return best
+
+
+def rigid_bench(device, n_rods=7744, tol=1e-4, reps=3):
+    """fcm_rigid_solve on the rod suspension of Section 6.1: n_rods rods of 22 particles (alternating
+    doublets, length 14.14a) on a square lattice, randomly oriented in the plane z = 30a of an
+    L x L x 60a box at the paper's 10.5% area fraction (L = 960a for 2,304 rods), each particle
+    under gravity F_0 x (no barrier forces at the lattice start), Broyden tolerance 1e-4 and fast
+    FCM at 1e-4 as in the paper, FP32. Times whole solves (synchronous; CUDA events on the stream)
+    and the fast-FCM product alone, checks the equations on the host (rigid particle velocities
+    under fcm_apply, rod force sums), and compares the rod velocities with an FP64 solve."""
+    import numpy as np
+    import torch
+    from paper_2310_12651_gb300 import fcm, inputs
+    L_xy, L_z = 960.0 * math.sqrt(n_rods / 2304.0), 60.0
+    Y, off, X = inputs.doublet_rods(n_rods, L_xy, L_z, 2310127500)
+    ft = inputs.rod_loads(n_rods, 2310127501, gravity=(1.0, 0.0, 0.0))
+    n = Y.shape[0]
+    pr = rod_suspension_params(L_xy, L_z, n, tol)
+    dev = torch.device("cuda", device)
+    st = torch.cuda.current_stream(dev)
+
+    def solve(prec, t):
+        dt = torch.float32 if prec == fcm.FCM_FP32 else torch.float64
+        tens = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+        pos, Xd, ftd = tens(Y), tens(X), tens(ft)
+        offd = torch.as_tensor(off, device=dev)
+        F = torch.zeros((n, 3), dtype=dt, device=dev)
+        UG = torch.zeros((n_rods, 6), dtype=dt, device=dev)
+        p = fcm.make_params((L_xy, L_xy, L_z), pr["M"], pr["Sigma"], pr["r_c"], pr["M_G"], n, prec)
+        out = {}
+        with fcm.Handle(p, device) as h:
+            _, it, res = h.rigid_solve(n, pos, n_rods, offd, Xd, ftd, F, UG, max_iter=256, tol=t,
+                                       stream=st.cuda_stream)
+            if prec == fcm.FCM_FP32:
+                times = []
+                for _ in range(reps):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(st)
+                    _, it, res = h.rigid_solve(n, pos, n_rods, offd, Xd, ftd, F, UG, max_iter=256, tol=t,
+                                               stream=st.cuda_stream)
+                    e1.record(st)
+                    e1.synchronize()
+                    times.append(e0.elapsed_time(e1))
+                V = torch.empty_like(F)
+                for _ in range(3):
+                    h.apply(n, pos, F, None, V, None, st.cuda_stream)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                for _ in range(reps * 4):
+                    h.apply(n, pos, F, None, V, None, st.cuda_stream)
+                e1.record(st)
+                e1.synchronize()
+                out["solve_ms"] = statistics.median(times)
+                out["apply_ms"] = e0.elapsed_time(e1) / (reps * 4)
+                out["V"] = V.double().cpu().numpy()
+            out.update(iterations=it, residual=res, F=F.double().cpu().numpy(), UG=UG.double().cpu().numpy())
+        return out
+
+    r32 = solve(fcm.FCM_FP32, tol)
+    r64 = solve(fcm.FCM_FP64, 1e-8)
+    # the equations on the host, body by body (22 particles each)
+    Lv = np.array([L_xy, L_xy, L_z])
+    Yr = Y.astype(np.float32).astype(np.float64).reshape(n_rods, 22, 3)
+    r = Yr - X.astype(np.float32).astype(np.float64)[:, None, :]
+    r -= Lv * np.round(r / Lv)
+    UG, F, V = r32["UG"], r32["F"].reshape(n_rods, 22, 3), r32["V"].reshape(n_rods, 22, 3)
+    rigid = UG[:, None, :3] + np.cross(UG[:, None, 3:], r)
+    sums = np.concatenate([F.sum(axis=1), np.cross(r, F).sum(axis=1)], axis=1)
+    it = r32["iterations"]
+    return {"workload": (f"{n_rods} rods x 22 particles (alternating doublets), square lattice, random in-plane "
+                         f"orientation, box {L_xy:.0f}a x {L_xy:.0f}a x {L_z:.0f}a (10.5% area fraction), "
+                         f"gravity F_0 x per particle, grid {pr['M'][0]}x{pr['M'][1]}x{pr['M'][2]}, "
+                         f"Sigma={pr['Sigma']:.3f}a, M_G={pr['M_G']}, r_c={pr['r_c']:.2f}a, FP32, "
+                         f"Broyden tol {tol:g}"),
+            "particles": n, "iterations": it, "relative_residual": r32["residual"],
+            "solve_ms": r32["solve_ms"], "ms_per_iteration": r32["solve_ms"] / max(it, 1),
+            "apply_ms": r32["apply_ms"],
+            "fcm_share_of_iteration": r32["apply_ms"] * it / r32["solve_ms"] if it else None,
+            "rod_solves_per_s": 1e3 / r32["solve_ms"],
+            "rigid_motion_rel": float(np.linalg.norm(V - rigid) / np.linalg.norm(V)),
+            "force_torque_sum_rel": float(np.linalg.norm(sums - ft) / np.linalg.norm(ft)),
+            "fp64_iterations_at_1e-8": r64["iterations"],
+            "rod_velocity_rel_l2_vs_fp64": float(np.linalg.norm(UG - r64["UG"]) / np.linalg.norm(r64["UG"]))}
+
+
 SERVE_CLASSES = 8          # box-size ladder of the serving mix (log-spaced L, one grid class each)
 SERVE_POOL = 32            # distinct systems drawn for the mix (half spheres, half 64-sphere rods)
 
@@ -547,6 +663,7 @@ def main():
     ap.add_argument("--no-sweep", action="store_true", help="skip the paper-settings PTPS sweep")
     ap.add_argument("--no-rods", action="store_true", help="skip the filament-layout measurement")
     ap.add_argument("--no-brownian", action="store_true", help="skip the Brownian-increment measurement")
+    ap.add_argument("--no-rigid", action="store_true", help="skip the rigid-rod mobility solve measurement")
     ap.add_argument("--sweep-full", action="store_true", help="include the 12.8%% (N = 1.96M) sweep row")
     ap.add_argument("--serve-requests", type=int, default=1024)
     ap.add_argument("--mode", default="batched", choices=["batched", "single"],
@@ -727,6 +844,7 @@ def main():
     sweep = None if args.no_sweep else paper_sweep(local, full=args.sweep_full)
     rods = None if args.no_rods else rods_bench(local)
     brown = None if args.no_brownian else brownian_bench(local)
+    rigid = None if args.no_rigid else rigid_bench(local)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -744,6 +862,7 @@ def main():
                    "d2h_bytes_per_step": B * 2 * n * 3 * 4},
            "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
            "fp64_plain": fp64, "serve": serve, "paper_sweep": sweep, "rods": rods, "brownian": brown,
+           "rigid_rods": rigid,
            "speedup_vs_fp64_plain": (value / world / fp64["value"]) if fp64 else None,
            "stages": stages_out, "step_ms_median": statistics.median(step_ms),
            "workspace_bytes": h.workspace_bytes()}

@@ -49,7 +49,8 @@ typedef enum fcm_status {
   FCM_ERR_TIMEOUT = 5,  /* a bounded wait ran out                                  */
   FCM_ERR_INPUT = 6,    /* the device flagged bad input (non-finite position)      */
   FCM_ERR_BUSY = 7,     /* the request is already running (fcm_server_cancel)      */
-  FCM_ERR_CANCELED = 8  /* the request was canceled before it ran                  */
+  FCM_ERR_CANCELED = 8, /* the request was canceled before it ran                  */
+  FCM_ERR_NOT_CONVERGED = 9 /* an iterative solve reached max_iter above its tolerance */
 } fcm_status;
 
 typedef enum fcm_precision {
@@ -148,6 +149,51 @@ int fcm_apply_stages(fcm_handle* h, int n, const void* pos, const void* F, const
 #define FCM_LANCZOS_MAX_ITER 64
 int fcm_brownian(fcm_handle* h, int n, const void* pos, double kT, const void* xi, const void* z, void* U, void* W,
                  int max_iter, double tol, int* iterations, void* stream);
+
+/* ---- Rigid bodies made of FCM particles (Section 6.1) -----------------------
+ * The rod suspensions of Section 6.1 build each rod from FCM particles that move
+ * as one rigid body. Body b owns particles body_off[b] .. body_off[b+1]-1, has
+ * reference point X_b and lever arms r_i = Y_i - X_b (minimum image). Given each
+ * body's force f_b and torque tau_b, fcm_rigid_solve finds the particle forces F
+ * and body velocities (U_b, Gamma_b) with
+ *   V = M^VF F               (fast-FCM product of forces only, eq. U)
+ *   V_i = U_b + Gamma_b x r_i                   (rigid motion, eq. ui)
+ *   sum_b F_i = f_b, sum_b r_i x F_i = tau_b    (eqs. Fn, Tn)
+ * by Broyden's method (inverse "good" update, full steps) started from the
+ * Jacobian of the diagonal mobility 1/(6 pi eta a) I, as the paper does. All
+ * vectors stay on the device; each iteration is one fast-FCM product plus a few
+ * vector kernels, and the host reads one residual norm per iteration.
+ * Unknowns x = (F, W / mu) and residual R = ((V - K W) / mu, K^T F - ft) with
+ * mu = 1/(6 pi eta a): both blocks in force units. Converged when
+ * ||R||_2 <= tol ||ft||_2.
+ *   n        : particles (0 < n <= max_n)
+ *   pos      : (n, 3) particle positions                               [device, read]
+ *   n_bodies : bodies (1 <= n_bodies <= n)
+ *   body_off : n_bodies + 1 ints, body_off[0] = 0, increasing, body_off[n_bodies]
+ *              = n; each body needs 3 particles not on one line (else its 6 x 6
+ *              K^T K is singular)                                   [device, read]
+ *   X        : (n_bodies, 3) reference points                          [device, read]
+ *   ft       : (n_bodies, 6) rows (f_b, tau_b)                         [device, read]
+ *   F        : (n, 3) particle forces                 [device, write; read if warm]
+ *   UG       : (n_bodies, 6) rows (U_b, Gamma_b)      [device, write; read if warm]
+ *   max_iter : 1 <= max_iter <= FCM_BROYDEN_MAX_ITER
+ *   tol      : relative residual tolerance (> 0; the paper uses 1e-4)
+ *   warm     : nonzero: start from the F and UG passed in (a previous step's
+ *              solution); zero: start from F = 0, UG = 0
+ *   iterations, residual : Broyden steps taken (one fast-FCM product each; a
+ *              warm start costs one more product) and the final ||R|| / ||ft||
+ *              (either may be NULL)
+ * Single-system use of any handle (system 0 of a batch handle), in the handle's
+ * precision. Synchronous. Allocates its workspace (about max_iter + 4 vectors of
+ * 3n + 6 n_bodies values) on first use and keeps it until fcm_destroy.
+ * FCM_ERR_INPUT if body_off is invalid or a body is degenerate (checked on the
+ * device before the first product); FCM_ERR_NOT_CONVERGED if max_iter products
+ * leave ||R|| above tol ||ft|| (F and UG then hold the last iterate). ft = 0 with
+ * warm = 0 returns F = 0, UG = 0 after 0 iterations. */
+#define FCM_BROYDEN_MAX_ITER 256
+int fcm_rigid_solve(fcm_handle* h, int n, const void* pos, int n_bodies, const int* body_off, const void* X,
+                    const void* ft, void* F, void* UG, int max_iter, double tol, int warm, int* iterations,
+                    double* residual, void* stream);
 
 /* ---- Batched systems (many independent systems in one pass) ----------------
  * The paper treats one periodic system at a time; running many small systems

@@ -228,6 +228,8 @@ struct fcm_handle {
   void* lz = nullptr;           // Lanczos basis and work vector (fcm_brownian), grown on demand
   size_t lz_bytes = 0;
   double* lz_dot = nullptr;     // device scalar of the Lanczos dot products
+  void* rg = nullptr;           // rigid-solve vectors, Broyden steps and scalars, grown on demand
+  size_t rg_bytes = 0;
   size_t bytes = 0;
   long long launches = 0;
   std::vector<void*> allocs;
@@ -274,6 +276,7 @@ void release(fcm_handle* h) {
   for (void* p : h->allocs) cudaFree(p);
   if (h->lz) cudaFree(h->lz);
   if (h->lz_dot) cudaFree(h->lz_dot);
+  if (h->rg) cudaFree(h->rg);
   delete h;
 }
 
@@ -869,6 +872,129 @@ int brownian(fcm_handle* h, int n, const R* pos, double kT, const R* xi, const R
   return FCM_OK;
 }
 
+// Rigid-body mobility solve (Section 6.1) by Broyden's method from the diagonal-mobility
+// Jacobian. Workspace carve-up of h->rg (256-byte aligned pieces):
+//   arm 3n R | ginv 36 nb double | x, z: m R | V 3n R | steps (max_iter + 1) x stride R |
+//   scalars: norm2[max_iter + 2], d rows (max_iter + 1) x ld, Gram rows (max_iter + 1) x ld,
+//   coef[ld], one, ftnorm2, flags[4]
+template <typename R>
+int rigid_solve(fcm_handle* h, int n, const R* pos, int nb, const int* body_off, const R* X, const R* ft, R* F,
+                R* UG, int max_iter, double tol, bool warm, int* iterations, double* residual, cudaStream_t s) {
+  const size_t m = 3 * (size_t)n + 6 * (size_t)nb;
+  const size_t stride = (m + 63) / 64 * 64;
+  const int ld = max_iter + 2;
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t b_arm = up(sizeof(R) * 3 * n), b_ginv = up(sizeof(double) * 36 * (size_t)nb);
+  const size_t b_vec = up(sizeof(R) * m), b_V = b_arm, b_S = sizeof(R) * stride * (size_t)(max_iter + 1);
+  const size_t n_scal = (size_t)ld + 2 * (size_t)(max_iter + 1) * ld + ld + 2;
+  const size_t b_scal = up(sizeof(double) * n_scal + 4 * sizeof(int));
+  const size_t need = b_arm + b_ginv + 2 * b_vec + b_V + up(b_S) + b_scal;
+  if (h->rg_bytes < need) {
+    if (h->rg) cudaFree(h->rg);
+    h->rg = nullptr;
+    h->rg_bytes = 0;
+    cudaError_t e = cudaMalloc(&h->rg, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(FCM_ERR_OOM, "rigid-solve workspace of " + std::to_string(need) + " bytes: " + cudaGetErrorString(e));
+    }
+    h->rg_bytes = need;
+  }
+  char* p = (char*)h->rg;
+  R* arm = (R*)p; p += b_arm;
+  double* ginv = (double*)p; p += b_ginv;
+  R* x = (R*)p; p += b_vec;
+  R* z = (R*)p; p += b_vec;
+  R* V = (R*)p; p += b_V;
+  R* S = (R*)p; p += up(b_S);
+  double* scal = (double*)p;
+  double* norm2 = scal;
+  double* drow = norm2 + ld;
+  double* gram = drow + (size_t)(max_iter + 1) * ld;
+  double* coef = gram + (size_t)(max_iter + 1) * ld;
+  double* one = coef + ld;
+  double* ftn2 = one + 1;
+  int* flags = (int*)(ftn2 + 1);
+  const double mu = 1.0 / (6.0 * kPi * h->p.eta * h->p.a);
+  const double onev = 1.0;
+  FCM_CUDA(cudaMemsetAsync(scal, 0, b_scal, s));
+  FCM_CUDA(cudaMemcpyAsync(one, &onev, sizeof(double), cudaMemcpyHostToDevice, s));
+  launch_rigid_setup<R>(pos, body_off, X, n, nb, h->p.L, arm, ginv, flags, s, &h->launches);
+  launch_dot<R>(ft, ft, 6 * (size_t)nb, ftn2, s, &h->launches);
+  int hf[4] = {0, 0, 0, 0};
+  double hft2 = 0.0;
+  FCM_CUDA(cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, s));
+  FCM_CUDA(cudaMemcpyAsync(&hft2, ftn2, sizeof(double), cudaMemcpyDeviceToHost, s));
+  FCM_CUDA(cudaStreamSynchronize(s));
+  if (hf[0]) return fail(FCM_ERR_INPUT, "body_off invalid at body " + std::to_string(hf[0] - 1));
+  if (hf[1])
+    return fail(FCM_ERR_INPUT, "body " + std::to_string(hf[1] - 1) + " is degenerate (K^T K singular: fewer than "
+                               "3 particles off one line)");
+  if (!std::isfinite(hft2)) return fail(FCM_ERR_INPUT, "ft is not finite");
+  const double tau = tol * std::sqrt(hft2);
+  int rc;
+  auto finish = [&](int it, double nrm2) -> int {
+    launch_axpby<R>(F, 1.0, x, 0.0, 3 * (size_t)n, s, &h->launches);
+    launch_axpby<R>(UG, mu, x + 3 * (size_t)n, 0.0, 6 * (size_t)nb, s, &h->launches);
+    FCM_CUDA(cudaGetLastError());
+    FCM_CUDA(cudaStreamSynchronize(s));
+    if (iterations) *iterations = it;
+    if (residual) *residual = hft2 > 0.0 ? std::sqrt(nrm2 / hft2) : std::sqrt(nrm2);
+    return FCM_OK;
+  };
+  if (!warm && hft2 == 0.0) {
+    launch_zero(x, sizeof(R) * m, s, &h->launches);
+    return finish(0, 0.0);
+  }
+  if (warm) {
+    launch_axpby<R>(x, 1.0, F, 0.0, 3 * (size_t)n, s, &h->launches);
+    launch_axpby<R>(x + 3 * (size_t)n, 1.0 / mu, UG, 0.0, 6 * (size_t)nb, s, &h->launches);
+    if ((rc = run<R>(h, 1, n, pos, x, nullptr, V, nullptr, FCM_STAGE_ALL, false, s))) return rc;
+  } else {
+    launch_zero(x, sizeof(R) * m, s, &h->launches);
+    launch_zero(V, sizeof(R) * 3 * (size_t)n, s, &h->launches);
+  }
+  auto read_norm = [&](int k, double* v, int* breakdown) -> int {
+    FCM_CUDA(cudaMemcpyAsync(v, norm2 + k, sizeof(double), cudaMemcpyDeviceToHost, s));
+    FCM_CUDA(cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, s));
+    FCM_CUDA(cudaStreamSynchronize(s));
+    *breakdown = hf[2];
+    return FCM_OK;
+  };
+  double nrm2 = 0.0;
+  int brk = 0;
+  launch_rigid_residual<R>(V, x, ft, arm, ginv, body_off, n, nb, 1.0 / mu, z, norm2, s, &h->launches);
+  if ((rc = read_norm(0, &nrm2, &brk))) return rc;
+  if (!std::isfinite(nrm2)) return fail(FCM_ERR_INPUT, "non-finite residual (check F and UG of a warm start)");
+  if (std::sqrt(nrm2) <= tau) return finish(0, nrm2);
+  // s_0 = z (coefficient 1), x += s_0, Gram row 0
+  launch_broyden_step<R>(z, S, m, stride, 0, one, S, x, s, &h->launches);
+  launch_multi_dot<R>(S, S, m, stride, 1, gram, s, &h->launches);
+  for (int it = 0; it < max_iter; ++it) {
+    const int nstep = it;   // steps s_0 .. s_nstep are stored, and x already includes s_nstep
+    if ((rc = run<R>(h, 1, n, pos, x, nullptr, V, nullptr, FCM_STAGE_ALL, false, s))) return rc;
+    launch_rigid_residual<R>(V, x, ft, arm, ginv, body_off, n, nb, 1.0 / mu, z, norm2 + it + 1, s, &h->launches);
+    if ((rc = read_norm(it + 1, &nrm2, &brk))) return rc;
+    if (!std::isfinite(nrm2)) return fail(FCM_ERR_INPUT, "non-finite residual in the Broyden iteration");
+    if (brk) {
+      finish(it + 1, nrm2);
+      return fail(FCM_ERR_NOT_CONVERGED, "Broyden update broke down (s_n . z = |s_n|^2) after " +
+                                             std::to_string(it + 1) + " iterations");
+    }
+    if (std::sqrt(nrm2) <= tau) return finish(it + 1, nrm2);
+    if (it + 1 == max_iter) break;
+    double* d = drow + (size_t)it * ld;
+    launch_multi_dot<R>(z, S, m, stride, nstep + 1, d, s, &h->launches);
+    launch_broyden_coef(d, gram, ld, nstep, coef, flags, s, &h->launches);
+    R* snext = S + (size_t)(nstep + 1) * stride;
+    launch_broyden_step<R>(z, S, m, stride, nstep, coef, snext, x, s, &h->launches);
+    launch_multi_dot<R>(snext, S, m, stride, nstep + 2, gram + (size_t)(nstep + 1) * ld, s, &h->launches);
+  }
+  if ((rc = finish(max_iter, nrm2))) return rc;
+  return fail(FCM_ERR_NOT_CONVERGED, "relative residual " + std::to_string(std::sqrt(nrm2 / hft2)) + " above tol " +
+                                         std::to_string(tol) + " after " + std::to_string(max_iter) + " iterations");
+}
+
 }  // namespace
 
 #pragma GCC visibility push(default)
@@ -893,6 +1019,30 @@ int fcm_brownian(fcm_handle* h, int n, const void* pos, double kT, const void* x
                             (double*)W, max_iter, tol, iterations, s);
   return brownian<float>(h, n, (const float*)pos, kT, (const float*)xi, (const float*)z, (float*)U, (float*)W,
                          max_iter, tol, iterations, s);
+}
+
+int fcm_rigid_solve(fcm_handle* h, int n, const void* pos, int n_bodies, const int* body_off, const void* X,
+                    const void* ft, void* F, void* UG, int max_iter, double tol, int warm, int* iterations,
+                    double* residual, void* stream) {
+  if (iterations) *iterations = 0;
+  if (residual) *residual = 0.0;
+  if (!h) return fail(FCM_ERR_ARG, "handle is NULL");
+  if (n < 1 || n > h->p.max_n)
+    return fail(FCM_ERR_ARG, "n = " + std::to_string(n) + " outside [1, max_n = " + std::to_string(h->p.max_n) + "]");
+  if (n_bodies < 1 || n_bodies > n)
+    return fail(FCM_ERR_ARG, "n_bodies = " + std::to_string(n_bodies) + " outside [1, n]");
+  if (max_iter < 1 || max_iter > FCM_BROYDEN_MAX_ITER)
+    return fail(FCM_ERR_ARG, "max_iter must be in [1, " + std::to_string(FCM_BROYDEN_MAX_ITER) + "]");
+  if (!(tol > 0.0) || !std::isfinite(tol)) return fail(FCM_ERR_ARG, "tol must be finite and > 0");
+  if (!pos || !body_off || !X || !ft || !F || !UG)
+    return fail(FCM_ERR_ARG, "pos, body_off, X, ft, F and UG must be non-NULL");
+  DeviceGuard guard(h->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (h->fp64)
+    return rigid_solve<double>(h, n, (const double*)pos, n_bodies, body_off, (const double*)X, (const double*)ft,
+                               (double*)F, (double*)UG, max_iter, tol, warm != 0, iterations, residual, s);
+  return rigid_solve<float>(h, n, (const float*)pos, n_bodies, body_off, (const float*)X, (const float*)ft,
+                            (float*)F, (float*)UG, max_iter, tol, warm != 0, iterations, residual, s);
 }
 
 }  // extern "C"

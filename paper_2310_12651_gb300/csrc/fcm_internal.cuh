@@ -300,6 +300,25 @@ template <typename R>   // out = sum_j c_j V[j] (+ out when accumulate), V[j] = 
 void launch_combine(R* out, const R* V, const LanczosCoef& c, int k, size_t m, bool accumulate, cudaStream_t s,
                     long long* launches);
 
+// Rigid-body solve (rigid.cu). Unknown and step vectors have length m = 3n + 6 nb, laid out
+// (F of n particles, W/mu of nb bodies); step j of the Broyden history sits at S + j * stride.
+constexpr int kBroydenMax = 256;
+template <typename R>   // lever arms (3n) and (K^T K)^-1 (36 nb); flags[0]: bad offsets, flags[1]: singular
+void launch_rigid_setup(const R* pos, const int* body_off, const R* X, int n, int nb, const double L[3], R* arm,
+                        double* ginv, int* flags, cudaStream_t s, long long* launches);
+template <typename R>   // z = -J0^-1 R(x) for V = M F, *norm2 += ||R||^2
+void launch_rigid_residual(const R* V, const R* x, const R* ft, const R* arm, const double* ginv, const int* body_off,
+                           int n, int nb, double inv_mu, R* z, double* norm2, cudaStream_t s, long long* launches);
+template <typename R>   // out[j] += a . (S + j stride), j < k
+void launch_multi_dot(const R* a, const R* S, size_t m, size_t stride, int k, double* out, cudaStream_t s,
+                      long long* launches);
+// coef of the next Broyden step from d (n + 1 values) and the Gram rows G (row stride ld); flags[2]: breakdown
+void launch_broyden_coef(const double* d, const double* G, int ld, int n, double* coef, int* flags, cudaStream_t s,
+                         long long* launches);
+template <typename R>   // s_out = coef[0] z + sum_{j<n} coef[1+j] S_{j+1}; x += s_out
+void launch_broyden_step(const R* z, const R* S, size_t m, size_t stride, int n, const double* coef, R* s_out, R* x,
+                         cudaStream_t s, long long* launches);
+
 // FP32 tiled spread / gather (tile accumulation, halo flush).
 size_t tile_smem_bytes(const int tile[3], int MG);      // extended region (gather, atomic spread)
 size_t spread_smem_bytes(const int tile[3], int MG);    // whichever spread kernel the tile selects

@@ -1,0 +1,327 @@
+// Kernels of the rigid-body mobility solve (rod suspensions, Section 6.1).
+//
+// Body b owns particles body_off[b] .. body_off[b+1]-1. The unknowns are
+// x = (F, W/mu) (3n + 6 n_bodies values, W rows (U_b, Gamma_b)); the residual is
+// R = ((V - K W)/mu, K^T F - ft) with V = M^VF F and (K W)_i = U_b + Gamma_b x r_i.
+// Broyden's method starts from the Jacobian of the diagonal mobility mu I,
+// J0 = [[I, -K], [K^T, 0]], whose inverse acts body by body:
+//     W = (K^T K)^-1 (r2 - K^T r1),  F = r1 + K W.
+// One warp per body computes the residual, its norm and -J0^-1 R in one pass; the
+// Broyden update itself is a Gram-matrix expansion of the product form
+// H_k = prod_j (I + s_{j+1} s_j^T / |s_j|^2) H0: per iteration one multi-dot
+// (z0 . s_j for every stored step), one warp of scalar recursion for the
+// coefficients, one multi-axpy writing the next step (and x += step), and one
+// multi-dot for the new row of the Gram matrix s_i . s_j.
+#include "fcm_internal.cuh"
+
+namespace fcm {
+
+namespace {
+
+constexpr int kBodyWarps = 8;   // bodies per 256-thread block
+
+__device__ inline double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum (blockDim.x == 256) of one value per thread, added atomically to *out by thread 0.
+__device__ inline void block_atomic_add(double v, double* out) {
+  __shared__ double part[8];
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+    atomicAdd(out, t);
+  }
+}
+
+// inv = A^-1 for a symmetric positive definite 6 x 6 A (row-major) by Cholesky;
+// false if a pivot falls below rel_tiny times its diagonal entry (singular body).
+__device__ bool invert_spd6(const double* A, double* inv, double rel_tiny) {
+  double Lc[6][6];
+  for (int j = 0; j < 6; ++j) {
+    double d = A[j * 6 + j];
+    for (int k = 0; k < j; ++k) d -= Lc[j][k] * Lc[j][k];
+    if (!(d > rel_tiny * A[j * 6 + j])) return false;
+    Lc[j][j] = sqrt(d);
+    for (int i = j + 1; i < 6; ++i) {
+      double v = A[i * 6 + j];
+      for (int k = 0; k < j; ++k) v -= Lc[i][k] * Lc[j][k];
+      Lc[i][j] = v / Lc[j][j];
+    }
+  }
+  for (int c = 0; c < 6; ++c) {
+    double y[6];
+    for (int i = 0; i < 6; ++i) {           // L y = e_c
+      double v = (i == c) ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) v -= Lc[i][k] * y[k];
+      y[i] = v / Lc[i][i];
+    }
+    for (int i = 5; i >= 0; --i) {          // L^T x = y
+      double v = y[i];
+      for (int k = i + 1; k < 6; ++k) v -= Lc[k][i] * y[k];
+      y[i] = v / Lc[i][i];
+    }
+    for (int i = 0; i < 6; ++i) inv[i * 6 + c] = y[i];
+  }
+  return true;
+}
+
+// Lever arms r_i = Y_i - X_b (minimum image, FP64) and (K^T K)^-1 of every body:
+// K^T K = [[n I, -[S]x], [[S]x, sum(|r|^2 I - r r^T)]] with S = sum r.
+// flags[0] <- 1 + first body with invalid offsets, flags[1] <- 1 + a singular body.
+template <typename R>
+__global__ void __launch_bounds__(256) rigid_setup_kernel(const R* __restrict__ pos, const int* __restrict__ body_off,
+                                                          const R* __restrict__ X, int n, int nb, double Lx,
+                                                          double Ly, double Lz, R* __restrict__ arm,
+                                                          double* __restrict__ ginv, int* flags) {
+  const int lane = threadIdx.x & 31;
+  const int b = blockIdx.x * kBodyWarps + (threadIdx.x >> 5);
+  if (b >= nb) return;   // whole warps leave together
+  const int o0 = body_off[b], o1 = body_off[b + 1];
+  if (o0 < 0 || o1 > n || o1 <= o0 || (b == 0 && o0 != 0) || (b == nb - 1 && o1 != n)) {
+    if (lane == 0) atomicCAS(&flags[0], 0, b + 1);
+    return;
+  }
+  const double xb = (double)X[3 * (size_t)b], yb = (double)X[3 * (size_t)b + 1], zb = (double)X[3 * (size_t)b + 2];
+  double s[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};   // Sx Sy Sz, then xx yy zz xy xz yz
+  for (int i = o0 + lane; i < o1; i += 32) {
+    double rx = (double)pos[3 * (size_t)i] - xb;
+    double ry = (double)pos[3 * (size_t)i + 1] - yb;
+    double rz = (double)pos[3 * (size_t)i + 2] - zb;
+    rx -= Lx * rint(rx / Lx);
+    ry -= Ly * rint(ry / Ly);
+    rz -= Lz * rint(rz / Lz);
+    arm[3 * (size_t)i] = (R)rx;
+    arm[3 * (size_t)i + 1] = (R)ry;
+    arm[3 * (size_t)i + 2] = (R)rz;
+    // the sums use the stored (rounded) arms, which every later kernel reads
+    rx = (double)(R)rx; ry = (double)(R)ry; rz = (double)(R)rz;
+    s[0] += rx; s[1] += ry; s[2] += rz;
+    s[3] += rx * rx; s[4] += ry * ry; s[5] += rz * rz;
+    s[6] += rx * ry; s[7] += rx * rz; s[8] += ry * rz;
+  }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) s[k] = warp_sum(s[k]);
+  if (lane != 0) return;
+  const double cnt = (double)(o1 - o0), tr = s[3] + s[4] + s[5];
+  double G[36];
+  for (int k = 0; k < 36; ++k) G[k] = 0.0;
+  G[0] = G[7] = G[14] = cnt;
+  // top right -[S]x, bottom left [S]x, [S]x = [[0, -Sz, Sy], [Sz, 0, -Sx], [-Sy, Sx, 0]]
+  const double Sx = s[0], Sy = s[1], Sz = s[2];
+  const double cx[9] = {0.0, -Sz, Sy, Sz, 0.0, -Sx, -Sy, Sx, 0.0};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      G[i * 6 + 3 + j] = -cx[i * 3 + j];
+      G[(3 + i) * 6 + j] = cx[i * 3 + j];
+    }
+  const double I[9] = {tr - s[3], -s[6], -s[7], -s[6], tr - s[4], -s[8], -s[7], -s[8], tr - s[5]};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) G[(3 + i) * 6 + 3 + j] = I[i * 3 + j];
+  if (!invert_spd6(G, ginv + 36 * (size_t)b, 1e-10)) {
+    atomicCAS(&flags[1], 0, b + 1);
+    for (int k = 0; k < 36; ++k) ginv[36 * (size_t)b + k] = 0.0;
+  }
+}
+
+// One warp per body: R1_i = V_i / mu - (W^_U + W^_G x r_i), R2 = (sum F - f, sum r x F - tau),
+// ||R||^2 added to *norm2, and z = -J0^-1 R written for the body's particles and its 6 values.
+template <typename R>
+__global__ void __launch_bounds__(256) rigid_residual_kernel(const R* __restrict__ V, const R* __restrict__ x,
+                                                             const R* __restrict__ ft, const R* __restrict__ arm,
+                                                             const double* __restrict__ ginv,
+                                                             const int* __restrict__ body_off, int n, int nb,
+                                                             double inv_mu, R* __restrict__ z,
+                                                             double* __restrict__ norm2) {
+  const int lane = threadIdx.x & 31;
+  const int b = blockIdx.x * kBodyWarps + (threadIdx.x >> 5);
+  double nr = 0.0;
+  if (b < nb) {
+    const int o0 = body_off[b], o1 = body_off[b + 1];
+    const R* wh = x + 3 * (size_t)n + 6 * (size_t)b;
+    double w[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) w[k] = (double)wh[k];
+    double acc[13];
+#pragma unroll
+    for (int k = 0; k < 13; ++k) acc[k] = 0.0;
+    for (int i = o0 + lane; i < o1; i += 32) {
+      const size_t q = 3 * (size_t)i;
+      const double rx = arm[q], ry = arm[q + 1], rz = arm[q + 2];
+      const double e0 = (double)V[q] * inv_mu - (w[0] + (w[4] * rz - w[5] * ry));
+      const double e1 = (double)V[q + 1] * inv_mu - (w[1] + (w[5] * rx - w[3] * rz));
+      const double e2 = (double)V[q + 2] * inv_mu - (w[2] + (w[3] * ry - w[4] * rx));
+      const double f0 = x[q], f1 = x[q + 1], f2 = x[q + 2];
+      acc[0] += e0; acc[1] += e1; acc[2] += e2;
+      acc[3] += ry * e2 - rz * e1; acc[4] += rz * e0 - rx * e2; acc[5] += rx * e1 - ry * e0;
+      acc[6] += f0; acc[7] += f1; acc[8] += f2;
+      acc[9] += ry * f2 - rz * f1; acc[10] += rz * f0 - rx * f2; acc[11] += rx * f1 - ry * f0;
+      acc[12] += e0 * e0 + e1 * e1 + e2 * e2;
+    }
+#pragma unroll
+    for (int k = 0; k < 13; ++k) acc[k] = warp_sum(acc[k]);
+    double r2[6], g[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      r2[k] = acc[6 + k] - (double)ft[6 * (size_t)b + k];
+      g[k] = r2[k] - acc[k];               // r2 - K^T r1
+    }
+    const double* gi = ginv + 36 * (size_t)b;
+    double y[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      double v = 0.0;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) v += gi[i * 6 + k] * g[k];
+      y[i] = v;
+    }
+    if (lane == 0) {
+      nr = acc[12];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        nr += r2[k] * r2[k];
+        z[3 * (size_t)n + 6 * (size_t)b + k] = (R)(-y[k]);
+      }
+    }
+    for (int i = o0 + lane; i < o1; i += 32) {
+      const size_t q = 3 * (size_t)i;
+      const double rx = arm[q], ry = arm[q + 1], rz = arm[q + 2];
+      const double e0 = (double)V[q] * inv_mu - (w[0] + (w[4] * rz - w[5] * ry));
+      const double e1 = (double)V[q + 1] * inv_mu - (w[1] + (w[5] * rx - w[3] * rz));
+      const double e2 = (double)V[q + 2] * inv_mu - (w[2] + (w[3] * ry - w[4] * rx));
+      z[q] = (R)(-(e0 + y[0] + (y[4] * rz - y[5] * ry)));
+      z[q + 1] = (R)(-(e1 + y[1] + (y[5] * rx - y[3] * rz)));
+      z[q + 2] = (R)(-(e2 + y[2] + (y[3] * ry - y[4] * rx)));
+    }
+  }
+  block_atomic_add(nr, norm2);
+}
+
+// out[j] += a . S_j for the k vectors S_j = S + j * stride (blockIdx.y = j).
+template <typename R>
+__global__ void __launch_bounds__(256) multi_dot_kernel(const R* __restrict__ a, const R* __restrict__ S, size_t m,
+                                                        size_t stride, double* __restrict__ out) {
+  const R* sj = S + (size_t)blockIdx.y * stride;
+  double v = 0.0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < m; e += (size_t)gridDim.x * blockDim.x)
+    v += (double)a[e] * (double)sj[e];
+  block_atomic_add(v, out + blockIdx.y);
+}
+
+// Coefficients of the next step from d_j = s_j . z0 (j <= n) and the Gram rows G[j][i] = s_j . s_i
+// (i <= j, row stride ld): with z_j = z0 + sum_{i<j} c_i s_{i+1},
+//     c_j = s_j . z_j / |s_j|^2 = (d_j + sum_{i<j} c_i G[j][i+1]) / G[j][j]       (j < n)
+//     s_{n+1} = z_n / (1 - s_n . z_n / |s_n|^2)
+// coef[0] multiplies z0 and coef[1 + j] multiplies s_{j+1}. One warp; flags[2] <- 1 on breakdown.
+__global__ void __launch_bounds__(32) broyden_coef_kernel(const double* __restrict__ d, const double* __restrict__ G,
+                                                          int ld, int n, double* __restrict__ coef, int* flags) {
+  __shared__ double c[kBroydenMax + 1];
+  const int lane = threadIdx.x;
+  double denom = 1.0;
+  for (int j = 0; j <= n; ++j) {
+    double t = 0.0;
+    for (int i = lane; i < j; i += 32) t += c[i] * G[(size_t)j * ld + i + 1];
+    t = warp_sum(t) + d[j];
+    const double gjj = G[(size_t)j * ld + j];
+    if (j < n) {
+      if (lane == 0) c[j] = t / gjj;
+      __syncwarp();
+    } else {
+      denom = 1.0 - t / gjj;
+    }
+  }
+  const bool ok = fabs(denom) > 1e-12 && isfinite(denom);
+  if (!ok && lane == 0) atomicCAS(&flags[2], 0, 1);
+  const double inv = ok ? 1.0 / denom : 0.0;
+  if (lane == 0) coef[0] = inv;
+  for (int j = lane; j < n; j += 32) coef[1 + j] = c[j] * inv;
+}
+
+// s_out = coef[0] z + sum_{j<n} coef[1+j] s_{j+1}, and x += s_out.
+template <typename R>
+__global__ void __launch_bounds__(256) broyden_step_kernel(const R* __restrict__ z, const R* __restrict__ S, size_t m,
+                                                           size_t stride, int n, const double* __restrict__ coef,
+                                                           R* __restrict__ s_out, R* __restrict__ x) {
+  __shared__ double c[kBroydenMax + 1];
+  for (int k = threadIdx.x; k <= n; k += blockDim.x) c[k] = coef[k];
+  __syncthreads();
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < m; e += (size_t)gridDim.x * blockDim.x) {
+    double v = c[0] * (double)z[e];
+    for (int j = 0; j < n; ++j) v += c[1 + j] * (double)S[(size_t)(j + 1) * stride + e];
+    const R sv = (R)v;
+    s_out[e] = sv;
+    x[e] = x[e] + sv;
+  }
+}
+
+int sm_count() {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
+
+int vec_blocks(size_t m) {
+  const size_t want = (m + 255) / 256;
+  const size_t cap = (size_t)sm_count() * 4;
+  return (int)std::max<size_t>(1, std::min(want, cap));
+}
+
+}  // namespace
+
+template <typename R>
+void launch_rigid_setup(const R* pos, const int* body_off, const R* X, int n, int nb, const double L[3], R* arm,
+                        double* ginv, int* flags, cudaStream_t s, long long* launches) {
+  const int blocks = (nb + kBodyWarps - 1) / kBodyWarps;
+  rigid_setup_kernel<R><<<blocks, 256, 0, s>>>(pos, body_off, X, n, nb, L[0], L[1], L[2], arm, ginv, flags);
+  *launches += 1;
+}
+
+template <typename R>
+void launch_rigid_residual(const R* V, const R* x, const R* ft, const R* arm, const double* ginv, const int* body_off,
+                           int n, int nb, double inv_mu, R* z, double* norm2, cudaStream_t s, long long* launches) {
+  const int blocks = (nb + kBodyWarps - 1) / kBodyWarps;
+  rigid_residual_kernel<R><<<blocks, 256, 0, s>>>(V, x, ft, arm, ginv, body_off, n, nb, inv_mu, z, norm2);
+  *launches += 1;
+}
+
+template <typename R>
+void launch_multi_dot(const R* a, const R* S, size_t m, size_t stride, int k, double* out, cudaStream_t s,
+                      long long* launches) {
+  // about 2 blocks per SM in total, at least one per vector
+  const int per = std::max(1, std::min(vec_blocks(m), (2 * sm_count() + k - 1) / k));
+  multi_dot_kernel<R><<<dim3(per, k), 256, 0, s>>>(a, S, m, stride, out);
+  *launches += 1;
+}
+
+void launch_broyden_coef(const double* d, const double* G, int ld, int n, double* coef, int* flags, cudaStream_t s,
+                         long long* launches) {
+  broyden_coef_kernel<<<1, 32, 0, s>>>(d, G, ld, n, coef, flags);
+  *launches += 1;
+}
+
+template <typename R>
+void launch_broyden_step(const R* z, const R* S, size_t m, size_t stride, int n, const double* coef, R* s_out, R* x,
+                         cudaStream_t s, long long* launches) {
+  broyden_step_kernel<R><<<vec_blocks(m), 256, 0, s>>>(z, S, m, stride, n, coef, s_out, x);
+  *launches += 1;
+}
+
+#define FCM_RIGID_INSTANTIATE(R)                                                                                    \
+  template void launch_rigid_setup<R>(const R*, const int*, const R*, int, int, const double[3], R*, double*, int*, \
+                                      cudaStream_t, long long*);                                                    \
+  template void launch_rigid_residual<R>(const R*, const R*, const R*, const R*, const double*, const int*, int, int, \
+                                         double, R*, double*, cudaStream_t, long long*);                            \
+  template void launch_multi_dot<R>(const R*, const R*, size_t, size_t, int, double*, cudaStream_t, long long*);    \
+  template void launch_broyden_step<R>(const R*, const R*, size_t, size_t, int, const double*, R*, R*, cudaStream_t, \
+                                       long long*);
+FCM_RIGID_INSTANTIATE(float)
+FCM_RIGID_INSTANTIATE(double)
+#undef FCM_RIGID_INSTANTIATE
+
+}  // namespace fcm

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfcm.so")
 
 (FCM_OK, FCM_ERR_ARG, FCM_ERR_OOM, FCM_ERR_CUDA, FCM_ERR_CUFFT, FCM_ERR_TIMEOUT, FCM_ERR_INPUT, FCM_ERR_BUSY,
- FCM_ERR_CANCELED) = range(9)
+ FCM_ERR_CANCELED, FCM_ERR_NOT_CONVERGED) = range(10)
 FCM_FP32, FCM_FP64 = 0, 1
 STAGE_GRID, STAGE_PAIR, STAGE_ALL = 1, 2, 3
 NUM_STAGES = 6
@@ -83,6 +83,7 @@ def _load():
         "fcm_batch_apply_stages": (i, [vp, i, ctypes.POINTER(i), vp, vp, vp, vp, vp, i, vp]),
         "fcm_max_systems": (i, [vp]),
         "fcm_brownian": (i, [vp, i, vp, d, vp, vp, vp, vp, i, d, ctypes.POINTER(i), vp]),
+        "fcm_rigid_solve": (i, [vp, i, vp, i, vp, vp, vp, vp, vp, i, d, i, ctypes.POINTER(i), ctypes.POINTER(d), vp]),
         "fcm_destroy": (i, [vp]),
         "fcm_apply": (i, [vp, i, vp, vp, vp, vp, vp, vp]),
         "fcm_apply_stages": (i, [vp, i, vp, vp, vp, vp, vp, i, vp]),
@@ -116,7 +117,8 @@ _lib = _load()
 #: symbols declared in include/fcm.h, for the export check
 EXPORTED = ("fcm_version", "fcm_params_default", "fcm_create", "fcm_destroy", "fcm_apply", "fcm_apply_stages",
             "fcm_create_batch", "fcm_batch_apply", "fcm_batch_apply_stages", "fcm_max_systems", "fcm_brownian",
-            "fcm_spread", "fcm_copy_grid", "fcm_check", "fcm_set_timing", "fcm_read_timing", "fcm_launch_count",
+            "fcm_rigid_solve", "fcm_spread", "fcm_copy_grid", "fcm_check", "fcm_set_timing", "fcm_read_timing",
+            "fcm_launch_count",
             "fcm_workspace_bytes", "fcm_cutoff_radius", "fcm_pair_correction_noalloc", "fcm_last_error",
             "fcm_server_create", "fcm_server_submit", "fcm_server_poll", "fcm_server_cancel", "fcm_server_get_stats",
             "fcm_server_reset_latency", "fcm_server_destroy")
@@ -125,6 +127,8 @@ EXPORTED = ("fcm_version", "fcm_params_default", "fcm_create", "fcm_destroy", "f
 MAX_BATCH = 1024
 #: most Lanczos iterations of fcm_brownian (include/fcm.h)
 LANCZOS_MAX_ITER = 64
+#: most Broyden iterations of fcm_rigid_solve (include/fcm.h)
+BROYDEN_MAX_ITER = 256
 
 #: capacity of fcm_pair_correction_noalloc's fixed scratch (include/fcm.h)
 NOALLOC_MAX_N = 65536
@@ -226,6 +230,20 @@ class Handle:
         _check(_lib.fcm_brownian(self._h, int(n), _ptr(pos), float(kT), _ptr(xi), _ptr(z), _ptr(U), _ptr(W),
                                  int(max_iter), float(tol), ctypes.byref(it), stream or None))
         return it.value
+
+    def rigid_solve(self, n, pos, n_bodies, body_off, X, ft, F, UG, max_iter=100, tol=1e-4, warm=False,
+                    stream=0, check=True):
+        """Rigid-body mobility solve (Broyden); returns (status, iterations, relative residual).
+
+        Raises FcmError on any status but FCM_OK, except FCM_ERR_NOT_CONVERGED when ``check`` is False.
+        """
+        it, res = ctypes.c_int(), ctypes.c_double()
+        code = _lib.fcm_rigid_solve(self._h, int(n), _ptr(pos), int(n_bodies), _ptr(body_off), _ptr(X), _ptr(ft),
+                                    _ptr(F), _ptr(UG), int(max_iter), float(tol), 1 if warm else 0,
+                                    ctypes.byref(it), ctypes.byref(res), stream or None)
+        if code != FCM_OK and (check or code != FCM_ERR_NOT_CONVERGED):
+            _check(code)
+        return code, it.value, res.value
 
     def spread(self, n, pos, F, T, stream=0):
         _check(_lib.fcm_spread(self._h, int(n), _ptr(pos), _ptr(F), _ptr(T), stream or None))

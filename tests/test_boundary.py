@@ -115,3 +115,22 @@ def test_server_rejects_bad_arguments_on_the_host(fcm, budget, max_batch, messag
     with pytest.raises(fcm.FcmError) as e:
         fcm.Server(hbm_budget=budget, max_batch=max_batch)
     assert e.value.code == fcm.FCM_ERR_ARG and message in str(e.value)
+
+
+def test_status_codes_match_header(fcm):
+    text = open(os.path.join(ROOT, "include", "fcm.h")).read()
+    codes = dict((k, int(v)) for k, v in re.findall(r"\b(FCM_(?:OK|ERR_[A-Z_]+))\s*=\s*(\d+)", text))
+    assert codes == {k: getattr(fcm, k) for k in codes} and codes["FCM_ERR_NOT_CONVERGED"] == 9
+    assert len(codes) == 10
+
+
+def test_rigid_solve_rejects_a_null_handle_on_the_host(fcm):
+    """Argument checks run before any CUDA call, so they work without a device."""
+    it, res = ctypes.c_int(7), ctypes.c_double(3.0)
+    lib = fcm.library()
+    code = lib.fcm_rigid_solve(None, 10, None, 1, None, None, None, None, None, 10, 1e-4, 0, ctypes.byref(it),
+                               ctypes.byref(res), None)
+    assert code == fcm.FCM_ERR_ARG and b"handle is NULL" in lib.fcm_last_error()
+    assert it.value == 0 and res.value == 0.0
+    assert fcm.BROYDEN_MAX_ITER == int(re.search(r"#define FCM_BROYDEN_MAX_ITER (\d+)",
+                                                 open(os.path.join(ROOT, "include", "fcm.h")).read()).group(1))
