@@ -657,8 +657,9 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--spread-kernel", type=int, default=0, help="0 choose, 1 row-stationary, 2 shared atomics")
     ap.add_argument("--tile", default="0,0,0", help="spread/gather tile x,y,z in grid points (0,0,0: the library's choice)")
-    ap.add_argument("--study", default=None, choices=["crossover"],
-                    help="run a study instead of the bench line: crossover = fast vs standard FCM against phi")
+    ap.add_argument("--study", default=None, choices=["crossover", "rigid", "brownian"],
+                    help="run one measurement instead of the bench line: crossover = fast vs standard FCM against "
+                         "phi; rigid = the rigid-rod solve on the 7,744-rod suspension; brownian = fcm_brownian")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-mix measurement")
     ap.add_argument("--no-sweep", action="store_true", help="skip the paper-settings PTPS sweep")
     ap.add_argument("--no-rods", action="store_true", help="skip the filament-layout measurement")
@@ -684,9 +685,10 @@ def main():
     from paper_2310_12651_gb300 import fcm, inputs
 
     torch.cuda.set_device(local)
-    if args.study == "crossover":
+    if args.study is not None:
+        run = {"crossover": crossover_study, "rigid": rigid_bench, "brownian": brownian_bench}[args.study]
         if rank == 0:
-            print(json.dumps({"study": "crossover", **crossover_study(local)}), flush=True)
+            print(json.dumps({"study": args.study, **run(local)}), flush=True)
         return 0
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()

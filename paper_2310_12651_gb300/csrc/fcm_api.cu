@@ -874,7 +874,7 @@ int brownian(fcm_handle* h, int n, const R* pos, double kT, const R* xi, const R
 
 // Rigid-body mobility solve (Section 6.1) by Broyden's method from the diagonal-mobility
 // Jacobian. Workspace carve-up of h->rg (256-byte aligned pieces):
-//   arm 3n R | ginv 36 nb double | x, z: m R | V 3n R | steps (max_iter + 1) x stride R |
+//   arm 3n R | ginv 36 nb R | x, z: m R | V 3n R | steps (max_iter + 1) x stride R |
 //   scalars: norm2[max_iter + 2], d rows (max_iter + 1) x ld, Gram rows (max_iter + 1) x ld,
 //   coef[ld], one, ftnorm2, flags[4]
 template <typename R>
@@ -884,7 +884,7 @@ int rigid_solve(fcm_handle* h, int n, const R* pos, int nb, const int* body_off,
   const size_t stride = (m + 63) / 64 * 64;
   const int ld = max_iter + 2;
   auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-  const size_t b_arm = up(sizeof(R) * 3 * n), b_ginv = up(sizeof(double) * 36 * (size_t)nb);
+  const size_t b_arm = up(sizeof(R) * 3 * n), b_ginv = up(sizeof(R) * 36 * (size_t)nb);
   const size_t b_vec = up(sizeof(R) * m), b_V = b_arm, b_S = sizeof(R) * stride * (size_t)(max_iter + 1);
   const size_t n_scal = (size_t)ld + 2 * (size_t)(max_iter + 1) * ld + ld + 2;
   const size_t b_scal = up(sizeof(double) * n_scal + 4 * sizeof(int));
@@ -902,7 +902,7 @@ int rigid_solve(fcm_handle* h, int n, const R* pos, int nb, const int* body_off,
   }
   char* p = (char*)h->rg;
   R* arm = (R*)p; p += b_arm;
-  double* ginv = (double*)p; p += b_ginv;
+  R* ginv = (R*)p; p += b_ginv;
   R* x = (R*)p; p += b_vec;
   R* z = (R*)p; p += b_vec;
   R* V = (R*)p; p += b_V;

@@ -305,9 +305,9 @@ void launch_combine(R* out, const R* V, const LanczosCoef& c, int k, size_t m, b
 constexpr int kBroydenMax = 256;
 template <typename R>   // lever arms (3n) and (K^T K)^-1 (36 nb); flags[0]: bad offsets, flags[1]: singular
 void launch_rigid_setup(const R* pos, const int* body_off, const R* X, int n, int nb, const double L[3], R* arm,
-                        double* ginv, int* flags, cudaStream_t s, long long* launches);
+                        R* ginv, int* flags, cudaStream_t s, long long* launches);
 template <typename R>   // z = -J0^-1 R(x) for V = M F, *norm2 += ||R||^2
-void launch_rigid_residual(const R* V, const R* x, const R* ft, const R* arm, const double* ginv, const int* body_off,
+void launch_rigid_residual(const R* V, const R* x, const R* ft, const R* arm, const R* ginv, const int* body_off,
                            int n, int nb, double inv_mu, R* z, double* norm2, cudaStream_t s, long long* launches);
 template <typename R>   // out[j] += a . (S + j stride), j < k
 void launch_multi_dot(const R* a, const R* S, size_t m, size_t stride, int k, double* out, cudaStream_t s,

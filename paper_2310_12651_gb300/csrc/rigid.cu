@@ -19,8 +19,10 @@ namespace fcm {
 namespace {
 
 constexpr int kBodyWarps = 8;   // bodies per 256-thread block
+constexpr int kCoefSmemMax = 200 * 1024;   // the coefficient kernel stages the Gram triangle up to this size
 
-__device__ inline double warp_sum(double v) {
+template <typename T>
+__device__ inline T warp_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
@@ -39,46 +41,16 @@ __device__ inline void block_atomic_add(double v, double* out) {
   }
 }
 
-// inv = A^-1 for a symmetric positive definite 6 x 6 A (row-major) by Cholesky;
-// false if a pivot falls below rel_tiny times its diagonal entry (singular body).
-__device__ bool invert_spd6(const double* A, double* inv, double rel_tiny) {
-  double Lc[6][6];
-  for (int j = 0; j < 6; ++j) {
-    double d = A[j * 6 + j];
-    for (int k = 0; k < j; ++k) d -= Lc[j][k] * Lc[j][k];
-    if (!(d > rel_tiny * A[j * 6 + j])) return false;
-    Lc[j][j] = sqrt(d);
-    for (int i = j + 1; i < 6; ++i) {
-      double v = A[i * 6 + j];
-      for (int k = 0; k < j; ++k) v -= Lc[i][k] * Lc[j][k];
-      Lc[i][j] = v / Lc[j][j];
-    }
-  }
-  for (int c = 0; c < 6; ++c) {
-    double y[6];
-    for (int i = 0; i < 6; ++i) {           // L y = e_c
-      double v = (i == c) ? 1.0 : 0.0;
-      for (int k = 0; k < i; ++k) v -= Lc[i][k] * y[k];
-      y[i] = v / Lc[i][i];
-    }
-    for (int i = 5; i >= 0; --i) {          // L^T x = y
-      double v = y[i];
-      for (int k = i + 1; k < 6; ++k) v -= Lc[k][i] * y[k];
-      y[i] = v / Lc[i][i];
-    }
-    for (int i = 0; i < 6; ++i) inv[i * 6 + c] = y[i];
-  }
-  return true;
-}
-
-// Lever arms r_i = Y_i - X_b (minimum image, FP64) and (K^T K)^-1 of every body:
-// K^T K = [[n I, -[S]x], [[S]x, sum(|r|^2 I - r r^T)]] with S = sum r.
+// Lever arms r_i = Y_i - X_b (minimum image, FP64) and (K^T K)^-1 of every body, one warp per body:
+// K^T K = [[n I, -[S]x], [[S]x, sum(|r|^2 I - r r^T)]] with S = sum r. Every lane factors the 6 x 6
+// matrix (Cholesky, FP64, registers); lanes 0..5 then solve for one column each. A pivot below
+// 1e-10 of its diagonal entry marks the body singular (fewer than 3 particles off one line).
 // flags[0] <- 1 + first body with invalid offsets, flags[1] <- 1 + a singular body.
 template <typename R>
 __global__ void __launch_bounds__(256) rigid_setup_kernel(const R* __restrict__ pos, const int* __restrict__ body_off,
                                                           const R* __restrict__ X, int n, int nb, double Lx,
                                                           double Ly, double Lz, R* __restrict__ arm,
-                                                          double* __restrict__ ginv, int* flags) {
+                                                          R* __restrict__ ginv, int* flags) {
   const int lane = threadIdx.x & 31;
   const int b = blockIdx.x * kBodyWarps + (threadIdx.x >> 5);
   if (b >= nb) return;   // whole warps leave together
@@ -107,36 +79,67 @@ __global__ void __launch_bounds__(256) rigid_setup_kernel(const R* __restrict__ 
   }
 #pragma unroll
   for (int k = 0; k < 9; ++k) s[k] = warp_sum(s[k]);
-  if (lane != 0) return;
   const double cnt = (double)(o1 - o0), tr = s[3] + s[4] + s[5];
-  double G[36];
-  for (int k = 0; k < 36; ++k) G[k] = 0.0;
-  G[0] = G[7] = G[14] = cnt;
-  // top right -[S]x, bottom left [S]x, [S]x = [[0, -Sz, Sy], [Sz, 0, -Sx], [-Sy, Sx, 0]]
   const double Sx = s[0], Sy = s[1], Sz = s[2];
-  const double cx[9] = {0.0, -Sz, Sy, Sz, 0.0, -Sx, -Sy, Sx, 0.0};
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) {
-      G[i * 6 + 3 + j] = -cx[i * 3 + j];
-      G[(3 + i) * 6 + j] = cx[i * 3 + j];
+  // G row-major; top right -[S]x, bottom left [S]x, [S]x = [[0, -Sz, Sy], [Sz, 0, -Sx], [-Sy, Sx, 0]]
+  const double G[36] = {cnt, 0.0, 0.0, 0.0,  Sz,  -Sy,
+                        0.0, cnt, 0.0, -Sz, 0.0,  Sx,
+                        0.0, 0.0, cnt,  Sy, -Sx, 0.0,
+                        0.0, -Sz,  Sy, tr - s[3], -s[6], -s[7],
+                         Sz, 0.0, -Sx, -s[6], tr - s[4], -s[8],
+                        -Sy,  Sx, 0.0, -s[7], -s[8], tr - s[5]};
+  double Lc[6][6];
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    double dgl = G[j * 6 + j];
+#pragma unroll
+    for (int k = 0; k < j; ++k) dgl -= Lc[j][k] * Lc[j][k];
+    ok = ok && (dgl > 1e-10 * G[j * 6 + j]);
+    Lc[j][j] = sqrt(fmax(dgl, 1e-300));
+#pragma unroll
+    for (int i = j + 1; i < 6; ++i) {
+      double v = G[i * 6 + j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) v -= Lc[i][k] * Lc[j][k];
+      Lc[i][j] = v / Lc[j][j];
     }
-  const double I[9] = {tr - s[3], -s[6], -s[7], -s[6], tr - s[4], -s[8], -s[7], -s[8], tr - s[5]};
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) G[(3 + i) * 6 + 3 + j] = I[i * 3 + j];
-  if (!invert_spd6(G, ginv + 36 * (size_t)b, 1e-10)) {
-    atomicCAS(&flags[1], 0, b + 1);
-    for (int k = 0; k < 36; ++k) ginv[36 * (size_t)b + k] = 0.0;
+  }
+  if (!ok) {
+    if (lane == 0) atomicCAS(&flags[1], 0, b + 1);
+    for (int k = lane; k < 36; k += 32) ginv[36 * (size_t)b + k] = R(0);
+    return;
+  }
+  if (lane < 6) {   // column c = lane of G^-1: L y = e_c, then L^T x = y
+    double y[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      double v = (i == lane) ? 1.0 : 0.0;
+#pragma unroll
+      for (int k = 0; k < i; ++k) v -= Lc[i][k] * y[k];
+      y[i] = v / Lc[i][i];
+    }
+#pragma unroll
+    for (int i = 5; i >= 0; --i) {
+      double v = y[i];
+#pragma unroll
+      for (int k = i + 1; k < 6; ++k) v -= Lc[k][i] * y[k];
+      y[i] = v / Lc[i][i];
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) ginv[36 * (size_t)b + i * 6 + lane] = (R)y[i];
   }
 }
 
-// One warp per body: R1_i = V_i / mu - (W^_U + W^_G x r_i), R2 = (sum F - f, sum r x F - tau),
-// ||R||^2 added to *norm2, and z = -J0^-1 R written for the body's particles and its 6 values.
+// One warp per body, in the handle's precision R: R1_i = V_i / mu - (W^_U + W^_G x r_i),
+// R2 = (sum F - f, sum r x F - tau), ||R||^2 added to *norm2 (FP64 across warps), and z = -J0^-1 R
+// written for the body's particles and its 6 values.
 template <typename R>
 __global__ void __launch_bounds__(256) rigid_residual_kernel(const R* __restrict__ V, const R* __restrict__ x,
                                                              const R* __restrict__ ft, const R* __restrict__ arm,
-                                                             const double* __restrict__ ginv,
+                                                             const R* __restrict__ ginv,
                                                              const int* __restrict__ body_off, int n, int nb,
-                                                             double inv_mu, R* __restrict__ z,
+                                                             R inv_mu, R* __restrict__ z,
                                                              double* __restrict__ norm2) {
   const int lane = threadIdx.x & 31;
   const int b = blockIdx.x * kBodyWarps + (threadIdx.x >> 5);
@@ -144,19 +147,19 @@ __global__ void __launch_bounds__(256) rigid_residual_kernel(const R* __restrict
   if (b < nb) {
     const int o0 = body_off[b], o1 = body_off[b + 1];
     const R* wh = x + 3 * (size_t)n + 6 * (size_t)b;
-    double w[6];
+    R w[6];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) w[k] = (double)wh[k];
-    double acc[13];
+    for (int k = 0; k < 6; ++k) w[k] = wh[k];
+    R acc[13];
 #pragma unroll
-    for (int k = 0; k < 13; ++k) acc[k] = 0.0;
+    for (int k = 0; k < 13; ++k) acc[k] = R(0);
     for (int i = o0 + lane; i < o1; i += 32) {
       const size_t q = 3 * (size_t)i;
-      const double rx = arm[q], ry = arm[q + 1], rz = arm[q + 2];
-      const double e0 = (double)V[q] * inv_mu - (w[0] + (w[4] * rz - w[5] * ry));
-      const double e1 = (double)V[q + 1] * inv_mu - (w[1] + (w[5] * rx - w[3] * rz));
-      const double e2 = (double)V[q + 2] * inv_mu - (w[2] + (w[3] * ry - w[4] * rx));
-      const double f0 = x[q], f1 = x[q + 1], f2 = x[q + 2];
+      const R rx = arm[q], ry = arm[q + 1], rz = arm[q + 2];
+      const R e0 = V[q] * inv_mu - (w[0] + (w[4] * rz - w[5] * ry));
+      const R e1 = V[q + 1] * inv_mu - (w[1] + (w[5] * rx - w[3] * rz));
+      const R e2 = V[q + 2] * inv_mu - (w[2] + (w[3] * ry - w[4] * rx));
+      const R f0 = x[q], f1 = x[q + 1], f2 = x[q + 2];
       acc[0] += e0; acc[1] += e1; acc[2] += e2;
       acc[3] += ry * e2 - rz * e1; acc[4] += rz * e0 - rx * e2; acc[5] += rx * e1 - ry * e0;
       acc[6] += f0; acc[7] += f1; acc[8] += f2;
@@ -165,69 +168,91 @@ __global__ void __launch_bounds__(256) rigid_residual_kernel(const R* __restrict
     }
 #pragma unroll
     for (int k = 0; k < 13; ++k) acc[k] = warp_sum(acc[k]);
-    double r2[6], g[6];
+    R r2[6], g[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-      r2[k] = acc[6 + k] - (double)ft[6 * (size_t)b + k];
+      r2[k] = acc[6 + k] - ft[6 * (size_t)b + k];
       g[k] = r2[k] - acc[k];               // r2 - K^T r1
     }
-    const double* gi = ginv + 36 * (size_t)b;
-    double y[6];
+    // y = (K^T K)^-1 g: lane i < 6 forms row i, then every lane takes the six values
+    R yi = R(0);
+    if (lane < 6) {
+      const R* gi = ginv + 36 * (size_t)b + 6 * lane;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      double v = 0.0;
-#pragma unroll
-      for (int k = 0; k < 6; ++k) v += gi[i * 6 + k] * g[k];
-      y[i] = v;
+      for (int k = 0; k < 6; ++k) yi += gi[k] * g[k];
     }
-    if (lane == 0) {
-      nr = acc[12];
+    R y[6];
 #pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        nr += r2[k] * r2[k];
-        z[3 * (size_t)n + 6 * (size_t)b + k] = (R)(-y[k]);
-      }
+    for (int k = 0; k < 6; ++k) y[k] = __shfl_sync(0xffffffffu, yi, k);
+    if (lane < 6) z[3 * (size_t)n + 6 * (size_t)b + lane] = -yi;
+    if (lane == 0) {
+      R t = acc[12];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) t += r2[k] * r2[k];
+      nr = (double)t;
     }
     for (int i = o0 + lane; i < o1; i += 32) {
       const size_t q = 3 * (size_t)i;
-      const double rx = arm[q], ry = arm[q + 1], rz = arm[q + 2];
-      const double e0 = (double)V[q] * inv_mu - (w[0] + (w[4] * rz - w[5] * ry));
-      const double e1 = (double)V[q + 1] * inv_mu - (w[1] + (w[5] * rx - w[3] * rz));
-      const double e2 = (double)V[q + 2] * inv_mu - (w[2] + (w[3] * ry - w[4] * rx));
-      z[q] = (R)(-(e0 + y[0] + (y[4] * rz - y[5] * ry)));
-      z[q + 1] = (R)(-(e1 + y[1] + (y[5] * rx - y[3] * rz)));
-      z[q + 2] = (R)(-(e2 + y[2] + (y[3] * ry - y[4] * rx)));
+      const R rx = arm[q], ry = arm[q + 1], rz = arm[q + 2];
+      const R e0 = V[q] * inv_mu - (w[0] + (w[4] * rz - w[5] * ry));
+      const R e1 = V[q + 1] * inv_mu - (w[1] + (w[5] * rx - w[3] * rz));
+      const R e2 = V[q + 2] * inv_mu - (w[2] + (w[3] * ry - w[4] * rx));
+      z[q] = -(e0 + y[0] + (y[4] * rz - y[5] * ry));
+      z[q + 1] = -(e1 + y[1] + (y[5] * rx - y[3] * rz));
+      z[q + 2] = -(e2 + y[2] + (y[3] * ry - y[4] * rx));
     }
   }
   block_atomic_add(nr, norm2);
 }
 
-// out[j] += a . S_j for the k vectors S_j = S + j * stride (blockIdx.y = j).
+// out[j] += a . S_j for the k vectors S_j = S + j * stride (blockIdx.y = j); each thread sums its
+// elements in R with four independent partial sums, blocks combine in FP64.
 template <typename R>
 __global__ void __launch_bounds__(256) multi_dot_kernel(const R* __restrict__ a, const R* __restrict__ S, size_t m,
                                                         size_t stride, double* __restrict__ out) {
   const R* sj = S + (size_t)blockIdx.y * stride;
-  double v = 0.0;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < m; e += (size_t)gridDim.x * blockDim.x)
-    v += (double)a[e] * (double)sj[e];
-  block_atomic_add(v, out + blockIdx.y);
+  const size_t step = (size_t)gridDim.x * blockDim.x;
+  size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  R v0 = R(0), v1 = R(0), v2 = R(0), v3 = R(0);
+  for (; e + 3 * step < m; e += 4 * step) {
+    v0 += a[e] * sj[e];
+    v1 += a[e + step] * sj[e + step];
+    v2 += a[e + 2 * step] * sj[e + 2 * step];
+    v3 += a[e + 3 * step] * sj[e + 3 * step];
+  }
+  for (; e < m; e += step) v0 += a[e] * sj[e];
+  block_atomic_add((double)((v0 + v1) + (v2 + v3)), out + blockIdx.y);
 }
 
 // Coefficients of the next step from d_j = s_j . z0 (j <= n) and the Gram rows G[j][i] = s_j . s_i
 // (i <= j, row stride ld): with z_j = z0 + sum_{i<j} c_i s_{i+1},
 //     c_j = s_j . z_j / |s_j|^2 = (d_j + sum_{i<j} c_i G[j][i+1]) / G[j][j]       (j < n)
 //     s_{n+1} = z_n / (1 - s_n . z_n / |s_n|^2)
-// coef[0] multiplies z0 and coef[1 + j] multiplies s_{j+1}. One warp; flags[2] <- 1 on breakdown.
+// coef[0] multiplies z0 and coef[1 + j] multiplies s_{j+1}. One warp; the lower triangle of G and d
+// are staged in shared memory first (all loads independent) when they fit (tri_smem), so the
+// sequential recursion reads shared memory. flags[2] <- 1 on breakdown.
 __global__ void __launch_bounds__(32) broyden_coef_kernel(const double* __restrict__ d, const double* __restrict__ G,
-                                                          int ld, int n, double* __restrict__ coef, int* flags) {
+                                                          int ld, int n, double* __restrict__ coef, int* flags,
+                                                          int tri_smem) {
+  extern __shared__ double tri[];   // rows 0..n of the triangle (row j: j + 1 values), then d
   __shared__ double c[kBroydenMax + 1];
   const int lane = threadIdx.x;
+  double* dsm = tri + (size_t)(n + 1) * (n + 2) / 2;
+  if (tri_smem) {
+    for (int j = 0; j <= n; ++j) {
+      const size_t rb = (size_t)j * (j + 1) / 2;
+      for (int k = lane; k <= j; k += 32) tri[rb + k] = G[(size_t)j * ld + k];
+    }
+    for (int j = lane; j <= n; j += 32) dsm[j] = d[j];
+    __syncwarp();
+  }
   double denom = 1.0;
   for (int j = 0; j <= n; ++j) {
+    const size_t rb = (size_t)j * (j + 1) / 2;
     double t = 0.0;
-    for (int i = lane; i < j; i += 32) t += c[i] * G[(size_t)j * ld + i + 1];
-    t = warp_sum(t) + d[j];
-    const double gjj = G[(size_t)j * ld + j];
+    for (int i = lane; i < j; i += 32) t += c[i] * (tri_smem ? tri[rb + i + 1] : G[(size_t)j * ld + i + 1]);
+    t = warp_sum(t) + (tri_smem ? dsm[j] : d[j]);
+    const double gjj = tri_smem ? tri[rb + j] : G[(size_t)j * ld + j];
     if (j < n) {
       if (lane == 0) c[j] = t / gjj;
       __syncwarp();
@@ -242,20 +267,19 @@ __global__ void __launch_bounds__(32) broyden_coef_kernel(const double* __restri
   for (int j = lane; j < n; j += 32) coef[1 + j] = c[j] * inv;
 }
 
-// s_out = coef[0] z + sum_{j<n} coef[1+j] s_{j+1}, and x += s_out.
+// s_out = coef[0] z + sum_{j<n} coef[1+j] s_{j+1}, and x += s_out (arithmetic in R).
 template <typename R>
 __global__ void __launch_bounds__(256) broyden_step_kernel(const R* __restrict__ z, const R* __restrict__ S, size_t m,
                                                            size_t stride, int n, const double* __restrict__ coef,
                                                            R* __restrict__ s_out, R* __restrict__ x) {
-  __shared__ double c[kBroydenMax + 1];
-  for (int k = threadIdx.x; k <= n; k += blockDim.x) c[k] = coef[k];
+  __shared__ R c[kBroydenMax + 1];
+  for (int k = threadIdx.x; k <= n; k += blockDim.x) c[k] = (R)coef[k];
   __syncthreads();
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < m; e += (size_t)gridDim.x * blockDim.x) {
-    double v = c[0] * (double)z[e];
-    for (int j = 0; j < n; ++j) v += c[1 + j] * (double)S[(size_t)(j + 1) * stride + e];
-    const R sv = (R)v;
-    s_out[e] = sv;
-    x[e] = x[e] + sv;
+    R v = c[0] * z[e];
+    for (int j = 0; j < n; ++j) v += c[1 + j] * S[(size_t)(j + 1) * stride + e];
+    s_out[e] = v;
+    x[e] = x[e] + v;
   }
 }
 
@@ -268,7 +292,7 @@ int sm_count() {
 
 int vec_blocks(size_t m) {
   const size_t want = (m + 255) / 256;
-  const size_t cap = (size_t)sm_count() * 4;
+  const size_t cap = (size_t)sm_count() * 8;
   return (int)std::max<size_t>(1, std::min(want, cap));
 }
 
@@ -276,32 +300,36 @@ int vec_blocks(size_t m) {
 
 template <typename R>
 void launch_rigid_setup(const R* pos, const int* body_off, const R* X, int n, int nb, const double L[3], R* arm,
-                        double* ginv, int* flags, cudaStream_t s, long long* launches) {
+                        R* ginv, int* flags, cudaStream_t s, long long* launches) {
   const int blocks = (nb + kBodyWarps - 1) / kBodyWarps;
   rigid_setup_kernel<R><<<blocks, 256, 0, s>>>(pos, body_off, X, n, nb, L[0], L[1], L[2], arm, ginv, flags);
   *launches += 1;
 }
 
 template <typename R>
-void launch_rigid_residual(const R* V, const R* x, const R* ft, const R* arm, const double* ginv, const int* body_off,
+void launch_rigid_residual(const R* V, const R* x, const R* ft, const R* arm, const R* ginv, const int* body_off,
                            int n, int nb, double inv_mu, R* z, double* norm2, cudaStream_t s, long long* launches) {
   const int blocks = (nb + kBodyWarps - 1) / kBodyWarps;
-  rigid_residual_kernel<R><<<blocks, 256, 0, s>>>(V, x, ft, arm, ginv, body_off, n, nb, inv_mu, z, norm2);
+  rigid_residual_kernel<R><<<blocks, 256, 0, s>>>(V, x, ft, arm, ginv, body_off, n, nb, (R)inv_mu, z, norm2);
   *launches += 1;
 }
 
 template <typename R>
 void launch_multi_dot(const R* a, const R* S, size_t m, size_t stride, int k, double* out, cudaStream_t s,
                       long long* launches) {
-  // about 2 blocks per SM in total, at least one per vector
-  const int per = std::max(1, std::min(vec_blocks(m), (2 * sm_count() + k - 1) / k));
+  // about 8 blocks per SM in total, at least one per vector
+  const int per = std::max(1, std::min(vec_blocks(m), (8 * sm_count() + k - 1) / k));
   multi_dot_kernel<R><<<dim3(per, k), 256, 0, s>>>(a, S, m, stride, out);
   *launches += 1;
 }
 
 void launch_broyden_coef(const double* d, const double* G, int ld, int n, double* coef, int* flags, cudaStream_t s,
                          long long* launches) {
-  broyden_coef_kernel<<<1, 32, 0, s>>>(d, G, ld, n, coef, flags);
+  const size_t bytes = sizeof(double) * ((size_t)(n + 1) * (n + 2) / 2 + (size_t)(n + 1));
+  const bool fits = bytes <= (size_t)kCoefSmemMax;
+  if (fits && bytes > 48 * 1024)   // beyond the default dynamic limit (set on the current device)
+    cudaFuncSetAttribute(broyden_coef_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kCoefSmemMax);
+  broyden_coef_kernel<<<1, 32, fits ? bytes : 0, s>>>(d, G, ld, n, coef, flags, fits ? 1 : 0);
   *launches += 1;
 }
 
@@ -313,9 +341,9 @@ void launch_broyden_step(const R* z, const R* S, size_t m, size_t stride, int n,
 }
 
 #define FCM_RIGID_INSTANTIATE(R)                                                                                    \
-  template void launch_rigid_setup<R>(const R*, const int*, const R*, int, int, const double[3], R*, double*, int*, \
+  template void launch_rigid_setup<R>(const R*, const int*, const R*, int, int, const double[3], R*, R*, int*,      \
                                       cudaStream_t, long long*);                                                    \
-  template void launch_rigid_residual<R>(const R*, const R*, const R*, const R*, const double*, const int*, int, int, \
+  template void launch_rigid_residual<R>(const R*, const R*, const R*, const R*, const R*, const int*, int, int,    \
                                          double, R*, double*, cudaStream_t, long long*);                            \
   template void launch_multi_dot<R>(const R*, const R*, size_t, size_t, int, double*, cudaStream_t, long long*);    \
   template void launch_broyden_step<R>(const R*, const R*, size_t, size_t, int, const double*, R*, R*, cudaStream_t, \
