@@ -19,7 +19,7 @@ namespace fcm {
 namespace {
 
 constexpr int kBodyWarps = 8;   // bodies per 256-thread block
-constexpr int kCoefSmemMax = 200 * 1024;   // the coefficient kernel stages the Gram triangle up to this size
+constexpr int kCoefSmemMax = 45 * 1024;   // Gram triangle staged up to this size (with the static 2 KB, under 48 KB)
 
 template <typename T>
 __device__ inline T warp_sum(T v) {
@@ -228,31 +228,35 @@ __global__ void __launch_bounds__(256) multi_dot_kernel(const R* __restrict__ a,
 // (i <= j, row stride ld): with z_j = z0 + sum_{i<j} c_i s_{i+1},
 //     c_j = s_j . z_j / |s_j|^2 = (d_j + sum_{i<j} c_i G[j][i+1]) / G[j][j]       (j < n)
 //     s_{n+1} = z_n / (1 - s_n . z_n / |s_n|^2)
-// coef[0] multiplies z0 and coef[1 + j] multiplies s_{j+1}. One warp; the lower triangle of G and d
-// are staged in shared memory first (all loads independent) when they fit (tri_smem), so the
-// sequential recursion reads shared memory. flags[2] <- 1 on breakdown.
+// coef[0] multiplies z0 and coef[1 + j] multiplies s_{j+1}. One warp; the lower triangle of G
+// (rows 0..n) and d are first copied to shared memory with independent loads when they fit in the
+// default 48 KB (gsm), so the sequential recursion reads shared memory. flags[2] <- 1 on breakdown.
 __global__ void __launch_bounds__(32) broyden_coef_kernel(const double* __restrict__ d, const double* __restrict__ G,
                                                           int ld, int n, double* __restrict__ coef, int* flags,
-                                                          int tri_smem) {
-  extern __shared__ double tri[];   // rows 0..n of the triangle (row j: j + 1 values), then d
+                                                          int gsm) {
+  extern __shared__ double blk[];   // triangle rows 0..n (row j: j + 1 values from offset j(j+1)/2), then d
   __shared__ double c[kBroydenMax + 1];
   const int lane = threadIdx.x;
-  double* dsm = tri + (size_t)(n + 1) * (n + 2) / 2;
-  if (tri_smem) {
-    for (int j = 0; j <= n; ++j) {
-      const size_t rb = (size_t)j * (j + 1) / 2;
-      for (int k = lane; k <= j; k += 32) tri[rb + k] = G[(size_t)j * ld + k];
+  const int tot = (n + 1) * (n + 2) / 2;
+  double* dsm = blk + tot;
+  if (gsm) {
+    for (int e = lane; e < tot; e += 32) {
+      int j = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);   // row of triangle entry e, then exact
+      while (j * (j + 1) / 2 > e) --j;
+      while ((j + 1) * (j + 2) / 2 <= e) ++j;
+      blk[e] = G[(size_t)j * ld + (e - j * (j + 1) / 2)];
     }
     for (int j = lane; j <= n; j += 32) dsm[j] = d[j];
     __syncwarp();
   }
+  const double* dr = gsm ? dsm : d;
   double denom = 1.0;
   for (int j = 0; j <= n; ++j) {
-    const size_t rb = (size_t)j * (j + 1) / 2;
+    const double* row = gsm ? blk + (size_t)j * (j + 1) / 2 : G + (size_t)j * ld;
     double t = 0.0;
-    for (int i = lane; i < j; i += 32) t += c[i] * (tri_smem ? tri[rb + i + 1] : G[(size_t)j * ld + i + 1]);
-    t = warp_sum(t) + (tri_smem ? dsm[j] : d[j]);
-    const double gjj = tri_smem ? tri[rb + j] : G[(size_t)j * ld + j];
+    for (int i = lane; i < j; i += 32) t += c[i] * row[i + 1];
+    t = warp_sum(t) + dr[j];
+    const double gjj = row[j];
     if (j < n) {
       if (lane == 0) c[j] = t / gjj;
       __syncwarp();
@@ -327,8 +331,6 @@ void launch_broyden_coef(const double* d, const double* G, int ld, int n, double
                          long long* launches) {
   const size_t bytes = sizeof(double) * ((size_t)(n + 1) * (n + 2) / 2 + (size_t)(n + 1));
   const bool fits = bytes <= (size_t)kCoefSmemMax;
-  if (fits && bytes > 48 * 1024)   // beyond the default dynamic limit (set on the current device)
-    cudaFuncSetAttribute(broyden_coef_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kCoefSmemMax);
   broyden_coef_kernel<<<1, 32, fits ? bytes : 0, s>>>(d, G, ld, n, coef, flags, fits ? 1 : 0);
   *launches += 1;
 }
