@@ -8,6 +8,10 @@
   1e-10 against the oracle at smaller sizes), the pair stage on sampled
   particles against the oracle computed one particle at a time, and the
   symmetry of the discrete operator.
+* Brownian increments on the 128^3 workload: the grid part at sampled particles against the
+  oracle's noise velocity on the whole grid.
+* The rigid-rod solve on the 7,744-rod suspension: the equations it solves, checked on the host,
+  and the rod velocities against an FP64 solve.
 """
 import numpy as np
 import pytest
@@ -74,3 +78,80 @@ def test_large_operator_symmetry(fcm, large):
     finally:
         large.F, large.T = F1, T1
     assert abs(a - b) < 1e-5 * (abs(a) + abs(b)), (a, b)
+
+
+def test_brownian_grid_part_full_size_on_sampled_particles(fcm):
+    """fcm_brownian's grid part on the 128^3 workload (the configuration bench.py times): the
+    noise through the square-root Stokes operator on the whole grid in the oracle, then
+    interpolated at 300 sampled particles, element by element."""
+    import torch
+    from oracle import brownian as ob
+    s = _workload(65536, 0.05, 128, 2.0, inputs.BASE_SEED + 1)
+    kT = 1.0
+    xi = np.random.default_rng(2310127400).standard_normal((3, 128, 128, 128))   # [c][z][y][x]
+    dev = torch.device("cuda:0")
+    pos = torch.as_tensor(s.Y, dtype=torch.float32, device=dev)
+    U = torch.empty_like(pos)
+    W = torch.empty_like(pos)
+    xid = torch.as_tensor(xi.ravel(), dtype=torch.float32, device=dev)
+    with fcm.Handle(fcm.make_params(s.L, s.M, s.Sigma, s.r_c, s.M_G, s.n, fcm.FCM_FP32)) as h:
+        it = h.brownian(s.n, pos, kT, xid, None, U, W, max_iter=10, tol=1e-6,
+                        stream=torch.cuda.current_stream().cuda_stream)
+    assert it == 0
+    idx = np.random.default_rng(75).choice(s.n, 300, replace=False)
+    xir = rounded(xi, fcm.FCM_FP32).transpose(0, 3, 2, 1)   # oracle layout [c][x][y][z]
+    h3 = (s.L / s.M) ** 3
+    u = np.sqrt(2.0 * kT / h3) * ob.grid_noise_velocity(xir, s.L)
+    Uo, Wo = og.interpolate(u, rounded(s.Y, fcm.FCM_FP32)[idx], s.L, s.M_G, s.Sigma, s.Sigma)
+    assert_parity(U.double().cpu().numpy()[idx], Uo, FP32_TOL, "U Brownian grid part, 300 of 65,536")
+    assert_parity(W.double().cpu().numpy()[idx], Wo, FP32_TOL, "W Brownian grid part, 300 of 65,536")
+
+
+def test_rod_suspension_rigid_solve_full_size(fcm):
+    """fcm_rigid_solve on the 7,744-rod suspension in the launch configuration bench.py times
+    (FP32, Broyden tol 1e-4): the equations it solves hold on the host (rigid particle velocities
+    under fcm_apply, rod force and torque sums), and the rod velocities agree with an FP64 solve at
+    1e-8 on the same GPU (the FP64 solve is held to the dense oracle at small sizes)."""
+    import math
+    import torch
+    import bench
+    n_rods, tol = 7744, 1e-4
+    Lxy, Lz = 960.0 * math.sqrt(n_rods / 2304.0), 60.0
+    Y, off, X = inputs.doublet_rods(n_rods, Lxy, Lz, 2310127500)
+    ft = inputs.rod_loads(n_rods, 2310127501, gravity=(1.0, 0.0, 0.0))
+    n = Y.shape[0]
+    pr = bench.rod_suspension_params(Lxy, Lz, n, tol)
+    dev = torch.device("cuda:0")
+    st = torch.cuda.current_stream().cuda_stream
+    out = {}
+    for prec, t in ((fcm.FCM_FP32, tol), (fcm.FCM_FP64, 1e-8)):
+        dt = torch.float32 if prec == fcm.FCM_FP32 else torch.float64
+        tens = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+        pos, Xd, ftd = tens(Y), tens(X), tens(ft)
+        F = torch.zeros((n, 3), dtype=dt, device=dev)
+        UG = torch.zeros((n_rods, 6), dtype=dt, device=dev)
+        p = fcm.make_params((Lxy, Lxy, Lz), pr["M"], pr["Sigma"], pr["r_c"], pr["M_G"], n, prec)
+        with fcm.Handle(p) as h:
+            code, it, res = h.rigid_solve(n, pos, n_rods, torch.as_tensor(off, device=dev), Xd, ftd, F, UG,
+                                          max_iter=256, tol=t, stream=st)
+            V = torch.empty_like(F)
+            h.apply(n, pos, F, None, V, None, st)
+            torch.cuda.synchronize()
+        assert code == fcm.FCM_OK and res <= t and it < 100, (prec, it, res)
+        out[prec] = (F.double().cpu().numpy(), UG.double().cpu().numpy(), V.double().cpu().numpy())
+    F, UG, V = out[fcm.FCM_FP32]
+    Lv = np.array([Lxy, Lxy, Lz])
+    r = rounded(Y, fcm.FCM_FP32).reshape(n_rods, 22, 3) - rounded(X, fcm.FCM_FP32)[:, None, :]
+    r -= Lv * np.round(r / Lv)
+    F3, V3 = F.reshape(n_rods, 22, 3), V.reshape(n_rods, 22, 3)
+    rigid = UG[:, None, :3] + np.cross(UG[:, None, 3:], r)
+    sums = np.concatenate([F3.sum(axis=1), np.cross(r, F3).sum(axis=1)], axis=1)
+    mu = 1.0 / (6.0 * math.pi)
+    # ||R|| <= tol ||ft||: the rigid-motion block times mu bounds the velocity residual
+    bound_v = tol * np.linalg.norm(ft) * mu / np.linalg.norm(V) * 1.01 + 3e-6
+    rel_v = float(np.linalg.norm(V3 - rigid) / np.linalg.norm(V))
+    rel_s = float(np.linalg.norm(sums - ft) / np.linalg.norm(ft))
+    print(f"7,744 rods: rigid-motion residual {rel_v:.2e} (bound {bound_v:.2e}), sums {rel_s:.2e}")
+    assert rel_v <= bound_v and rel_s <= tol * 1.01 + 3e-6
+    # rod velocities: the FP32 solve at 1e-4 against the FP64 solve at 1e-8
+    assert rel_l2(UG, out[fcm.FCM_FP64][1]) <= 1e-4
