@@ -15,7 +15,7 @@ namespace fcm {
 
 constexpr unsigned kFullMask32 = 0xffffffffu;
 constexpr int kRowsMaxThreads = 512;   // row-stationary spread: one thread per extended (y, z) row
-constexpr int kRowsChunk = 32;         // particles staged per pass
+constexpr int kRowsChunk = 64;         // particles staged per pass
 
 // Shared layout of the extended region: row pitch P (odd) and plane pitch Q
 // with Q = P M_G (mod 32), so the 32 lanes of a warp, which own 32 consecutive
