@@ -357,10 +357,11 @@ def crossover_study(device, a_over_L=(0.012, 0.008), tols=(1e-4, 1e-6),
     return {"rows": rows, "crossings": crossings}
 
 
-def brownian_bench(device, reps=5, tol=1e-6):
+def brownian_bench(device, reps=5, tol=1e-6, with_oracle=False):
     """fcm_brownian on one system of the 128^3 workload (N = 65,536, phi = 5%, Sigma = 2a, FP32): the
     grid part (noise -> square-root Stokes projection -> interpolation) and the Lanczos pair part,
-    each timed on its own (the call is synchronous; host wall clock around the call)."""
+    each timed on its own (the call is synchronous; host wall clock around the call). with_oracle: the
+    oracle timed beside it on a bounded sample."""
     import numpy as np
     import torch
     from paper_2310_12651_gb300 import fcm, inputs
@@ -387,6 +388,23 @@ def brownian_bench(device, reps=5, tol=1e-6):
     out["workload"] = (f"one system of N={n}, phi=5%, {M}^3, Sigma=2a, M_G={w['M_G']}, r_c={w['r_c']:.2f}a, FP32, "
                        f"Lanczos tol {tol:g}; synchronous call timed on the host")
     out["particle_increments_per_s"] = n / ((out["grid_part"]["ms"] + out["pair_part"]["ms"]) * 1e-3)
+    if with_oracle:   # the oracle as it stands (exact matrix square root of the pair part) on a bounded sample
+        from oracle import brownian as ob
+        ns = 600
+        ws = workload("c2", n=ns, h_ref=w["h"])
+        Ys = inputs.random_suspension(ns, ws["L"], inputs.BASE_SEED + 5)
+        xis = rng.standard_normal((3, ws["M"], ws["M"], ws["M"]))
+        zs = rng.standard_normal((ns, 3))
+        t0 = time.perf_counter()
+        ob.brownian_grid(Ys, xis, ws["L"], ws["M_G"], ws["Sigma"], ws["Sigma"], 1.0)
+        t1 = time.perf_counter()
+        ob.brownian_pair(Ys, zs, ws["L"], ws["r_c"], ws["Sigma"], 1.0)
+        t2 = time.perf_counter()
+        out["oracle"] = {"kind": "oracle", "cores": 1, "grid_part_ms": (t1 - t0) * 1e3, "pair_part_ms": (t2 - t1) * 1e3,
+                         "particle_increments_per_s": ns / (t2 - t0),
+                         "sample": f"N={ns} at phi=5% (L={ws['L']:.1f}a, {ws['M']}^3, h={ws['h']:.3f}a, Sigma=2a, "
+                                   f"M_G={ws['M_G']}, r_c={ws['r_c']:.2f}a), FP64 "
+                                   f"numpy single thread; pair part by dense eigendecomposition"}
     return out
 
 
@@ -423,14 +441,35 @@ def rod_suspension_params(L_xy, L_z, n, tol, precision=None):
     return best
 
 
-def rigid_bench(device, n_rods=7744, tol=1e-4, reps=3):
+def rigid_oracle_sample(tol, n_rods=16):
+    """The oracle's rigid-body Broyden (fast-FCM oracle product, FP64 numpy) on n_rods rods at the
+    10.5% area fraction of the rod suspension (box 960a sqrt(n_rods / 2304) x same x 60a)."""
+    from oracle import rigid as orr
+    from paper_2310_12651_gb300 import inputs
+    L_xy, L_z = 960.0 * math.sqrt(n_rods / 2304.0), 60.0
+    Y, off, X = inputs.doublet_rods(n_rods, L_xy, L_z, 2310127510)
+    ft = inputs.rod_loads(n_rods, 2310127511, gravity=(1.0, 0.0, 0.0))
+    pr = rod_suspension_params(L_xy, L_z, Y.shape[0], tol)
+    t0 = time.perf_counter()
+    _, _, it, _ = orr.fast_fcm_rigid_broyden(Y, off, X, ft, (L_xy, L_xy, L_z), pr["M"], pr["M_G"], pr["Sigma"],
+                                             pr["r_c"], tol, 256)
+    secs = time.perf_counter() - t0
+    return {"kind": "oracle", "cores": 1, "iterations": it, "solve_s": secs,
+            "particle_iterations_per_s": Y.shape[0] * max(it, 1) / secs,
+            "sample": f"{n_rods} rods x 22 particles, box {L_xy:.0f}a x {L_xy:.0f}a x {L_z:.0f}a, grid "
+                      f"{pr['M'][0]}x{pr['M'][1]}x{pr['M'][2]}, Broyden tol {tol:g}, FP64 numpy single thread"}
+
+
+def rigid_bench(device, n_rods=7744, tol=1e-4, reps=3, with_oracle=False):
     """fcm_rigid_solve on the rod suspension of Section 6.1: n_rods rods of 22 particles (alternating
     doublets, length 14.14a) on a square lattice, randomly oriented in the plane z = 30a of an
     L x L x 60a box at the paper's 10.5% area fraction (L = 960a for 2,304 rods), each particle
     under gravity F_0 x (no barrier forces at the lattice start), Broyden tolerance 1e-4 and fast
     FCM at 1e-4 as in the paper, FP32. Times whole solves (synchronous; CUDA events on the stream)
     and the fast-FCM product alone, checks the equations on the host (rigid particle velocities
-    under fcm_apply, rod force sums), and compares the rod velocities with an FP64 solve."""
+    under fcm_apply, rod force sums), and compares the rod velocities with an FP64 solve. with_oracle:
+    the oracle's Broyden (fast-FCM oracle product) timed beside it on 16 rods at the same area
+    fraction."""
     import numpy as np
     import torch
     from paper_2310_12651_gb300 import fcm, inputs
@@ -500,9 +539,11 @@ def rigid_bench(device, n_rods=7744, tol=1e-4, reps=3):
             "apply_ms": r32["apply_ms"],
             "fcm_share_of_iteration": r32["apply_ms"] * it / r32["solve_ms"] if it else None,
             "rod_solves_per_s": 1e3 / r32["solve_ms"],
+            "particle_iterations_per_s": n * max(it, 1) / (r32["solve_ms"] * 1e-3),
             "rigid_motion_rel": float(np.linalg.norm(V - rigid) / np.linalg.norm(V)),
             "force_torque_sum_rel": float(np.linalg.norm(sums - ft) / np.linalg.norm(ft)),
             "fp64_iterations_at_1e-8": r64["iterations"],
+            "oracle": rigid_oracle_sample(tol) if with_oracle else None,
             "rod_velocity_rel_l2_vs_fp64": float(np.linalg.norm(UG - r64["UG"]) / np.linalg.norm(r64["UG"]))}
 
 
@@ -686,9 +727,13 @@ def main():
 
     torch.cuda.set_device(local)
     if args.study is not None:
-        run = {"crossover": crossover_study, "rigid": rigid_bench, "brownian": brownian_bench}[args.study]
         if rank == 0:
-            print(json.dumps({"study": args.study, **run(local)}), flush=True)
+            if args.study == "crossover":
+                res = crossover_study(local)
+            else:
+                run = {"rigid": rigid_bench, "brownian": brownian_bench}[args.study]
+                res = run(local, with_oracle=not args.no_cpu_baseline)
+            print(json.dumps({"study": args.study, **res}), flush=True)
         return 0
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
@@ -845,8 +890,9 @@ def main():
         serve = serve_bench(local, requests=args.serve_requests)
     sweep = None if args.no_sweep else paper_sweep(local, full=args.sweep_full)
     rods = None if args.no_rods else rods_bench(local)
-    brown = None if args.no_brownian else brownian_bench(local)
-    rigid = None if args.no_rigid else rigid_bench(local)
+    oracle_here = rank == 0 and world == 1 and not args.no_cpu_baseline
+    brown = None if args.no_brownian else brownian_bench(local, with_oracle=oracle_here)
+    rigid = None if args.no_rigid else rigid_bench(local, with_oracle=oracle_here)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
