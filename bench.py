@@ -460,6 +460,23 @@ def rigid_oracle_sample(tol, n_rods=16):
                       f"{pr['M'][0]}x{pr['M'][1]}x{pr['M'][2]}, Broyden tol {tol:g}, FP64 numpy single thread"}
 
 
+def rigid_roofline(stages, n, M_G, device):
+    """FP32 ALU roofline of the spread inside the rigid solve: forces only, 12 flops per window point
+    (three components, two FMA each), against 152 SMs x 128 lanes x 2 x the maximum SM clock."""
+    import torch
+    ms, cnt = stages.get("spread", (0.0, 0))
+    if not cnt:
+        return None
+    sm_count = torch.cuda.get_device_properties(device).multi_processor_count
+    sm_max = peaks().get("sm_max_mhz") or 2070.0
+    peak = sm_count * 128 * 2 * sm_max * 1e6 / 1e12
+    achieved = 12.0 * n * M_G ** 3 / (ms / cnt * 1e-3) / 1e12
+    return {"bound": "alu", "kernel": "spread", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "spread_ms_per_launch": ms / cnt,
+            "stage_share": {k: v[0] / sum(x[0] for kk, x in stages.items() if kk != "apply")
+                            for k, v in stages.items() if k != "apply"}}
+
+
 def rigid_bench(device, n_rods=7744, tol=1e-4, reps=3, with_oracle=False):
     """fcm_rigid_solve on the rod suspension of Section 6.1: n_rods rods of 22 particles (alternating
     doublets, length 14.14a) on a square lattice, randomly oriented in the plane z = 30a of an
@@ -513,6 +530,12 @@ def rigid_bench(device, n_rods=7744, tol=1e-4, reps=3, with_oracle=False):
                 e1.record(st)
                 e1.synchronize()
                 out["solve_ms"] = statistics.median(times)
+                # per-stage CUDA-event times over one more solve: the spread's roofline inside the solve
+                h.set_timing(True)
+                h.read_timing()
+                h.rigid_solve(n, pos, n_rods, offd, Xd, ftd, F, UG, max_iter=256, tol=t, stream=st.cuda_stream)
+                out["stages"] = {k: v for k, v in h.read_timing().items() if v[1]}
+                h.set_timing(False)
                 out["apply_ms"] = e0.elapsed_time(e1) / (reps * 4)
                 out["V"] = V.double().cpu().numpy()
             out.update(iterations=it, residual=res, F=F.double().cpu().numpy(), UG=UG.double().cpu().numpy())
@@ -540,6 +563,7 @@ def rigid_bench(device, n_rods=7744, tol=1e-4, reps=3, with_oracle=False):
             "fcm_share_of_iteration": r32["apply_ms"] * it / r32["solve_ms"] if it else None,
             "rod_solves_per_s": 1e3 / r32["solve_ms"],
             "particle_iterations_per_s": n * max(it, 1) / (r32["solve_ms"] * 1e-3),
+            "roofline": rigid_roofline(r32["stages"], n, pr["M_G"], device),
             "rigid_motion_rel": float(np.linalg.norm(V - rigid) / np.linalg.norm(V)),
             "force_torque_sum_rel": float(np.linalg.norm(sums - ft) / np.linalg.norm(ft)),
             "fp64_iterations_at_1e-8": r64["iterations"],
