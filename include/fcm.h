@@ -355,8 +355,9 @@ int fcm_server_destroy(fcm_server* s);
 
 /* The pairwise and self corrections (M - M~)(F, T) of one FP32 system, like
  * fcm_apply_stages(..., FCM_STAGE_PAIR), for callers that cannot allocate
- * device memory (an allocator or arena that owns the device, code running
- * while a graph is captured, hosts that forbid cudaMalloc after start-up).
+ * device memory: code whose memory pool or arena owns the whole device (a
+ * cudaMalloc beside it would fail or fragment the pool), and hosts that
+ * allocate everything at start-up and forbid cudaMalloc afterwards.
  * The paper has no counterpart: this entry point exists for those callers.
  *   p      : L, a, eta, Sigma, Sigma_D, r_c of the system (precision must be
  *            FCM_FP32; M, M_G, max_n and tile are not used)

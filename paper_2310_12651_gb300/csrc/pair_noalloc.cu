@@ -1,8 +1,9 @@
 // Pair correction with no device allocation.
 //
 // Some callers cannot allocate device memory: code that runs inside a memory
-// pool or arena that owns the whole device, code called while a CUDA graph is
-// being captured, or host environments that forbid cudaMalloc after start-up.
+// pool or arena that owns the whole device (a cudaMalloc beside it would fail
+// or fragment the pool), or host environments that allocate everything at
+// start-up and forbid cudaMalloc afterwards.
 // fcm_pair_correction_noalloc serves them: it computes the pairwise and self
 // corrections (M - M~)(F, T) of one FP32 system with the library's binning and
 // pair kernels, and keeps every intermediate (sort keys, cell lists, sorted

@@ -1,9 +1,10 @@
 """The pair correction through the entry point that allocates no device memory.
 
-Callers that cannot allocate device memory (an allocator that owns the whole
-device, code running while a CUDA graph is captured, hosts that forbid
-cudaMalloc after start-up) call fcm_pair_correction_noalloc, which keeps all
-its scratch in one fixed device array. Its result must match the pair stage of
+Callers that cannot allocate device memory (code whose memory pool owns the
+whole device, so that a cudaMalloc beside it fails or fragments the pool, and
+hosts that allocate everything at start-up and forbid cudaMalloc afterwards)
+call fcm_pair_correction_noalloc, which keeps all its scratch in one fixed
+device array. Its result must match the pair stage of
 the handle-based entry point (fcm_apply_stages with FCM_STAGE_PAIR) within the
 FP32 tolerance of the parity tests, on two calls in a row with different loads
 (so a second call cannot pass on what the first left behind). The file is
