@@ -51,3 +51,22 @@ def test_workload_parameters_match_the_documented_rules():
     assert abs(w["r_c"] - params.cutoff_radius(2.0, 1e-6, torques=True)) < 1e-6
     small = bench.workload("c2", n=16384, h_ref=w["h"])
     assert abs(small["h"] - w["h"]) / w["h"] < 0.02 and small["M_G"] == 14
+
+
+@pytest.mark.parametrize("n_rods, tol", [(7744, 1e-4), (2304, 1e-4), (16, 1e-4), (2304, 1e-6)])
+def test_rod_suspension_parameters_follow_the_rules(n_rods, tol):
+    """The rod-suspension parameters: Sigma resolved at the tolerance's Table 1 ratio on the coarser
+    spacing, the window rule for M_G, FFT-friendly even grids, and a cutoff inside half the 60a height."""
+    import math
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2310_12651_gb300 import tune
+    L_xy, L_z = 960.0 * math.sqrt(n_rods / 2304.0), 60.0
+    pr = bench.rod_suspension_params(L_xy, L_z, 22 * n_rods, tol)
+    Mx, My, Mz = pr["M"]
+    h = max(L_xy / Mx, L_z / Mz)
+    assert Mx == My and all(m % 2 == 0 and tune._smooth(m) for m in pr["M"])
+    assert pr["Sigma"] / h >= tune.resolution_for(tune.GRID_SHARE * tol) - 1e-12
+    assert pr["M_G"] == tune.support_points(pr["Sigma"], min(L_xy / Mx, L_z / Mz), tune.truncation_for(tune.GRID_SHARE * tol))
+    assert 0 < pr["r_c"] <= 0.5 * L_z and pr["M_G"] <= min(24, Mz)
+    assert pr["r_c"] >= tune.cutoff(pr["Sigma"], 0.5 * tol, torques=False) - 1e-9
