@@ -62,55 +62,62 @@ __global__ void __launch_bounds__(256) gather_tile_kernel(Geometry<float> g, Ker
       gx1[j] = dj * gdj;
     }
     float u0 = 0.f, u1 = 0.f, u2 = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f;
-    int jy = lane, jz = 0;
-    if (GUARD) {
-      while (jy >= MG) { jy -= MG; ++jz; }
-    }
-    for (int r0 = 0; r0 < MG * MG; r0 += 32) {
-      if (!GUARD) {  // window row r = jy + M_G jz, division by a compile-time constant
-        jz = (r0 + lane) / MGT;
-        jy = r0 + lane - jz * MGT;
-      }
-      const bool active = r0 + lane < MG * MG;
-      const int sy = active ? jy : 0, sz = active ? jz : 0;
+    // one window row (jy, jz) of this particle: x sums over the row, times the row's y, z factors
+    auto row_update = [&](const float* row, int sy, int sz, bool active) {
       const float dy = __shfl_sync(kFullMask32, dyl, sy);
       const float gy = __shfl_sync(kFullMask32, gyl, sy);
       const float dz = __shfl_sync(kFullMask32, dzl, sz);
       const float gz = __shfl_sync(kFullMask32, gzl, sz);
       const float gdy = SAMEW ? gy : __shfl_sync(kFullMask32, gdyl, sy);
       const float gdz = SAMEW ? gz : __shfl_sync(kFullMask32, gdzl, sz);
-      if (active) {
-        const float* row = acc + (off.z + jz) * l.Q + (off.y + jy) * l.P + off.x;
-        float sx0 = 0.f, sy0 = 0.f, sz0 = 0.f, sx2 = 0.f, sy2 = 0.f, sz2 = 0.f;
-        float dx0 = 0.f, dy0 = 0.f, dz0 = 0.f, dy1 = 0.f, dz1 = 0.f;
+      if (!active) return;
+      float sx0 = 0.f, sy0 = 0.f, sz0 = 0.f, sx2 = 0.f, sy2 = 0.f, sz2 = 0.f;
+      float dx0 = 0.f, dy0 = 0.f, dz0 = 0.f, dy1 = 0.f, dz1 = 0.f;
 #pragma unroll
-        for (int j = 0; j < MGT; ++j) {
-          if (!GUARD || j < MG) {
-            const float ux = row[j], uy = row[l.C + j], uz = row[2 * l.C + j];
-            sx0 = fmaf(gx[j], ux, sx0); sy0 = fmaf(gx[j], uy, sy0); sz0 = fmaf(gx[j], uz, sz0);
-            sx2 = fmaf(gx2[j], ux, sx2); sy2 = fmaf(gx2[j], uy, sy2); sz2 = fmaf(gx2[j], uz, sz2);
-            if (TORQUE) {
-              if (!SAMEW) { dx0 = fmaf(gdx[j], ux, dx0); dy0 = fmaf(gdx[j], uy, dy0); dz0 = fmaf(gdx[j], uz, dz0); }
-              dy1 = fmaf(gx1[j], uy, dy1);
-              dz1 = fmaf(gx1[j], uz, dz1);
-            }
+      for (int j = 0; j < MGT; ++j) {
+        if (!GUARD || j < MG) {
+          const float ux = row[j], uy = row[l.C + j], uz = row[2 * l.C + j];
+          sx0 = fmaf(gx[j], ux, sx0); sy0 = fmaf(gx[j], uy, sy0); sz0 = fmaf(gx[j], uz, sz0);
+          sx2 = fmaf(gx2[j], ux, sx2); sy2 = fmaf(gx2[j], uy, sy2); sz2 = fmaf(gx2[j], uz, sz2);
+          if (TORQUE) {
+            if (!SAMEW) { dx0 = fmaf(gdx[j], ux, dx0); dy0 = fmaf(gdx[j], uy, dy0); dz0 = fmaf(gdx[j], uz, dz0); }
+            dy1 = fmaf(gx1[j], uy, dy1);
+            dz1 = fmaf(gx1[j], uz, dz1);
           }
         }
-        const float G = kc.nrm * gy * gz;
-        const float GQ = G * fmaf(kc.B, fmaf(dy, dy, dz * dz), kc.A);
-        const float GB = G * kc.B;
-        u0 = fmaf(GQ, sx0, fmaf(GB, sx2, u0));
-        u1 = fmaf(GQ, sy0, fmaf(GB, sy2, u1));
-        u2 = fmaf(GQ, sz0, fmaf(GB, sz2, u2));
-        if (TORQUE) {
-          if (SAMEW) { dx0 = sx0; dy0 = sy0; dz0 = sz0; }
-          const float H = kc.tq * gdy * gdz;
-          w0 = fmaf(H, dy * dz0 - dz * dy0, w0);
-          w1 = fmaf(H, dz * dx0 - dz1, w1);
-          w2 = fmaf(H, dy1 - dy * dx0, w2);
-        }
       }
-      if (GUARD) {
+      const float G = kc.nrm * gy * gz;
+      const float GQ = G * fmaf(kc.B, fmaf(dy, dy, dz * dz), kc.A);
+      const float GB = G * kc.B;
+      u0 = fmaf(GQ, sx0, fmaf(GB, sx2, u0));
+      u1 = fmaf(GQ, sy0, fmaf(GB, sy2, u1));
+      u2 = fmaf(GQ, sz0, fmaf(GB, sz2, u2));
+      if (TORQUE) {
+        if (SAMEW) { dx0 = sx0; dy0 = sy0; dz0 = sz0; }
+        const float H = kc.tq * gdy * gdz;
+        w0 = fmaf(H, dy * dz0 - dz * dy0, w0);
+        w1 = fmaf(H, dz * dx0 - dz1, w1);
+        w2 = fmaf(H, dy1 - dy * dx0, w2);
+      }
+    };
+    if (!GUARD) {
+      // window row r = jy + M_G jz of lane and pass it: fixed per lane, so the row offsets inside the
+      // staged region (jz Q + jy P) are loop invariants of the particle loop
+      const float* pbase = acc + off.z * l.Q + off.y * l.P + off.x;
+#pragma unroll
+      for (int it = 0; it < (MGT * MGT + 31) / 32; ++it) {
+        const int r = 32 * it + lane;
+        const bool active = r < MGT * MGT;
+        const int jz = active ? r / MGT : 0, jy = active ? r - (r / MGT) * MGT : 0;
+        row_update(pbase + jz * l.Q + jy * l.P, jy, jz, active);
+      }
+    } else {
+      int jy = lane, jz = 0;
+      while (jy >= MG) { jy -= MG; ++jz; }
+      for (int r0 = 0; r0 < MG * MG; r0 += 32) {
+        const bool active = r0 + lane < MG * MG;
+        const int sy = active ? jy : 0, sz = active ? jz : 0;
+        row_update(acc + (off.z + sz) * l.Q + (off.y + sy) * l.P + off.x, sy, sz, active);
         jy += 32;
         while (jy >= MG) { jy -= MG; ++jz; }
       }
