@@ -104,12 +104,53 @@ __global__ void __launch_bounds__(256) gather_tile_kernel(Geometry<float> g, Ker
       // window row r = jy + M_G jz of lane and pass it: fixed per lane, so the row offsets inside the
       // staged region (jz Q + jy P) are loop invariants of the particle loop
       const float* pbase = acc + off.z * l.Q + off.y * l.P + off.x;
+      constexpr int NFULL = MGT * MGT / 32, TAIL = MGT * MGT % 32;
+      constexpr bool SPLIT_TAIL = TAIL > 0 && TAIL * MGT <= 64;   // a short last pass: split it by points
 #pragma unroll
-      for (int it = 0; it < (MGT * MGT + 31) / 32; ++it) {
+      for (int it = 0; it < (SPLIT_TAIL ? NFULL : (MGT * MGT + 31) / 32); ++it) {
         const int r = 32 * it + lane;
         const bool active = r < MGT * MGT;
         const int jz = active ? r / MGT : 0, jy = active ? r - (r / MGT) * MGT : 0;
         row_update(pbase + jz * l.Q + jy * l.P, jy, jz, active);
+      }
+      if (SPLIT_TAIL) {
+        // the last TAIL rows have TAIL * M_G (row, point) items: each lane takes up to two and applies
+        // the row's y, z factors to each item itself
+#pragma unroll
+        for (int pass = 0; pass < 2; ++pass) {
+          const int e = lane + 32 * pass;
+          const bool valid = e < TAIL * MGT;
+          const int t = valid ? e / MGT : 0, j = valid ? e - (e / MGT) * MGT : 0;
+          const int r = 32 * NFULL + t;
+          const int jz = r / MGT, jy = r - jz * MGT;
+          const float gj = __shfl_sync(kFullMask32, gxl, j);
+          const float dj = __shfl_sync(kFullMask32, dxl, j);
+          const float gdj = SAMEW ? gj : __shfl_sync(kFullMask32, gdxl, j);
+          const float dy = __shfl_sync(kFullMask32, dyl, jy);
+          const float gy = __shfl_sync(kFullMask32, gyl, jy);
+          const float dz = __shfl_sync(kFullMask32, dzl, jz);
+          const float gz = __shfl_sync(kFullMask32, gzl, jz);
+          const float gdy = SAMEW ? gy : __shfl_sync(kFullMask32, gdyl, jy);
+          const float gdz = SAMEW ? gz : __shfl_sync(kFullMask32, gdzl, jz);
+          if (valid) {
+            const float* row = pbase + jz * l.Q + jy * l.P;
+            const float ux = row[j], uy = row[l.C + j], uz = row[2 * l.C + j];
+            const float G = kc.nrm * gy * gz;
+            const float GQ = G * fmaf(kc.B, fmaf(dy, dy, dz * dz), kc.A);
+            const float GB = G * kc.B;
+            const float wgt = fmaf(GB, dj * dj * gj, GQ * gj);
+            u0 = fmaf(wgt, ux, u0);
+            u1 = fmaf(wgt, uy, u1);
+            u2 = fmaf(wgt, uz, u2);
+            if (TORQUE) {
+              const float H = kc.tq * gdy * gdz;
+              const float g1 = dj * gdj;
+              w0 = fmaf(H, gdj * (dy * uz - dz * uy), w0);
+              w1 = fmaf(H, dz * gdj * ux - g1 * uz, w1);
+              w2 = fmaf(H, g1 * uy - dy * gdj * ux, w2);
+            }
+          }
+        }
       }
     } else {
       int jy = lane, jz = 0;
