@@ -8,6 +8,8 @@
   1e-10 against the oracle at smaller sizes), the pair stage on sampled
   particles against the oracle computed one particle at a time, and the
   symmetry of the discrete operator.
+* The exact batched launch bench.py times (32 systems of the 128^3 workload): sampled systems
+  against their single-system applies, and the last one against the full oracle.
 * Brownian increments on the 128^3 workload: the grid part at sampled particles against the
   oracle's noise velocity on the whole grid.
 * The rigid-rod solve on the 7,744-rod suspension: the equations it solves, checked on the host,
@@ -155,3 +157,37 @@ def test_rod_suspension_rigid_solve_full_size(fcm):
     assert rel_v <= bound_v and rel_s <= tol * 1.01 + 3e-6
     # rod velocities: the FP32 solve at 1e-4 against the FP64 solve at 1e-8
     assert rel_l2(UG, out[fcm.FCM_FP64][1]) <= 1e-4
+
+
+def test_bench_launch_configuration_32_systems(fcm):
+    """The batched pass bench.py times (32 systems x N = 65,536 at 5%, 128^3, Sigma = 2a, the bench's
+    seeds, one fcm_batch_apply): every sampled system equals its single-system apply (atomic rounding
+    only, 1e-6), and the last system matches the full FP64 oracle element by element."""
+    import torch
+    import bench
+    w = bench.workload("c2")
+    n, B = w["n"], 32
+    systems = [System(n, w["L"], w["M"], w["Sigma"], w["M_G"], w["r_c"], 0,
+                      Y=inputs.random_suspension(n, w["L"], inputs.BASE_SEED + 1 + 100 * b)) for b in range(B)]
+    for b, s in enumerate(systems):   # the bench's loads: seed + 1 of each system
+        s.F, s.T = inputs.random_loads(n, inputs.BASE_SEED + 2 + 100 * b)
+    dev = torch.device("cuda:0")
+    st = torch.cuda.current_stream().cuda_stream
+    cat = lambda attr: torch.as_tensor(np.concatenate([getattr(s, attr) for s in systems]), dtype=torch.float32,
+                                       device=dev)
+    pos, F, T = cat("Y"), cat("F"), cat("T")
+    U = torch.empty_like(F)
+    W = torch.empty_like(F)
+    offsets = [b * n for b in range(B + 1)]
+    p = fcm.make_params(w["L"], w["M"], w["Sigma"], w["r_c"], w["M_G"], n * B, fcm.FCM_FP32)
+    with fcm.Handle(p, 0, max_systems=B) as h:
+        h.batch_apply(offsets, pos, F, T, U, W, st)
+        assert h.check() == 0
+    Ub, Wb = U.double().cpu().numpy(), W.double().cpu().numpy()
+    for b in (0, 13, 31):
+        Us, Ws = run_gpu(systems[b], fcm.FCM_FP32)
+        assert_parity(Ub[b * n:(b + 1) * n], Us, 1e-6, f"U system {b} of the batch vs alone")
+        assert_parity(Wb[b * n:(b + 1) * n], Ws, 1e-6, f"W system {b} of the batch vs alone")
+    Uo, Wo = systems[31].oracle(fcm.FCM_FP32)
+    assert_parity(Ub[31 * n:], Uo, FP32_TOL, "U system 31 of the batch vs oracle")
+    assert_parity(Wb[31 * n:], Wo, FP32_TOL, "W system 31 of the batch vs oracle")
