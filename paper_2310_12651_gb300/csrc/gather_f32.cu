@@ -8,9 +8,10 @@
 // One CTA per tile: the extended region of u is copied into shared memory with
 // asynchronous 4-byte copies (no register round trip), then a warp owns a
 // particle and its lanes own window rows; the M_G x-profiles are computed by
-// M_G lanes and broadcast into registers with warp shuffles. Per point: 3
-// shared loads and 8 FMA. The pair-correction sums, when present, are added
-// when U and W are written in input order.
+// M_G lanes and broadcast into registers with warp shuffles. Per point: a 4-byte
+// load (x) and an 8-byte load (y, z interleaved) from shared memory and 8 FMA.
+// The pair-correction sums, when present, are added when U and W are written
+// in input order.
 #include "grid_common.cuh"
 
 namespace fcm {
@@ -76,7 +77,9 @@ __global__ void __launch_bounds__(256) gather_tile_kernel(Geometry<float> g, Ker
 #pragma unroll
       for (int j = 0; j < MGT; ++j) {
         if (!GUARD || j < MG) {
-          const float ux = row[j], uy = row[l.C + j], uz = row[2 * l.C + j];
+          const float ux = row[j];
+          const float2 uyz = reinterpret_cast<const float2*>(acc + yz_plane_offset(l))[(row - acc) + j];
+          const float uy = uyz.x, uz = uyz.y;
           sx0 = fmaf(gx[j], ux, sx0); sy0 = fmaf(gx[j], uy, sy0); sz0 = fmaf(gx[j], uz, sz0);
           sx2 = fmaf(gx2[j], ux, sx2); sy2 = fmaf(gx2[j], uy, sy2); sz2 = fmaf(gx2[j], uz, sz2);
           if (TORQUE) {
@@ -134,7 +137,9 @@ __global__ void __launch_bounds__(256) gather_tile_kernel(Geometry<float> g, Ker
           const float gdz = SAMEW ? gz : __shfl_sync(kFullMask32, gdzl, jz);
           if (valid) {
             const float* row = pbase + jz * l.Q + jy * l.P;
-            const float ux = row[j], uy = row[l.C + j], uz = row[2 * l.C + j];
+            const float ux = row[j];
+          const float2 uyz = reinterpret_cast<const float2*>(acc + yz_plane_offset(l))[(row - acc) + j];
+          const float uy = uyz.x, uz = uyz.y;
             const float G = kc.nrm * gy * gz;
             const float GQ = G * fmaf(kc.B, fmaf(dy, dy, dz * dz), kc.A);
             const float GB = G * kc.B;

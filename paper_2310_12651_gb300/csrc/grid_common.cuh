@@ -86,10 +86,16 @@ __device__ inline int4 window_offset(const Geometry<float>& g, const TileOrigin&
   return off;
 }
 
+// Offset (floats) of the interleaved (y, z) plane of the gather's staged region: after the x
+// plane, rounded up to 8 bytes.
+__host__ __device__ inline int yz_plane_offset(const ExtLayout& l) { return (l.C + 1) & ~1; }
+
 // Copies the extended region of the grid (3 components) into shared memory with
 // asynchronous 4-byte copies: warps take (component, z) planes, lanes take x,
 // rows advance by pointer increments (the y range is split at its periodic wrap,
-// so no per-row wrap test).
+// so no per-row wrap test). Layout: the x component as one plane (index
+// ez Q + ey P + ex), then the y and z components interleaved as float2 at the
+// same index from yz_plane_offset, so the gather reads them with one 8-byte load.
 __device__ inline void stage_region_async(const Geometry<float>& g, const TileOrigin& o, const ExtLayout& l,
                                           const float* __restrict__ grid, float* ext) {
   const size_t Mtot = (size_t)g.M[0] * g.M[1] * g.M[2];
@@ -104,8 +110,10 @@ __device__ inline void stage_region_async(const Geometry<float>& g, const TileOr
       const int ez = pl - c * l.EZ;
       const int gz = wrap_index(o.oz0 + ez, g.M[2]);
       const float* gplane = grid + c * Mtot + (size_t)gz * g.M[1] * g.M[0] + gx;
-      unsigned sa = (unsigned)__cvta_generic_to_shared(ext + c * l.C + ez * l.Q + lane);
-      const unsigned sstep = 4u * (unsigned)l.P;
+      const int idx = ez * l.Q + lane;
+      float* dst = c == 0 ? ext + idx : ext + yz_plane_offset(l) + 2 * idx + (c - 1);
+      unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+      const unsigned sstep = (c == 0 ? 4u : 8u) * (unsigned)l.P;
       // rows gy0 .. gy0 + n1 - 1, then rows 0 .. EY - n1 - 1: pointers advance by one row each
       const float* src = gplane + (size_t)gy0 * row;
 #pragma unroll 4

@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(256) spread_tile_kernel(Geometry<float> g, Ker
 
 size_t tile_smem_bytes(const int tile[3], int MG) {
   const ExtLayout l = ext_layout(tile, MG);
-  return sizeof(float) * 3 * (size_t)l.C;
+  return sizeof(float) * (3 * (size_t)l.C + 1);   // + 1: the gather's (y, z) plane starts 8-byte aligned
 }
 
 int tile_smem_limit() { return 227 * 1024; }
