@@ -17,7 +17,8 @@ rod's force and torque and the problem is the saddle-point system
 Its exact solution (dense LU, or the Schur complement) is the oracle for the GPU
 solve. The paper solves it with Broyden's method started from the Jacobian of a
 diagonal mobility M = mu I, mu = 1/(6 pi eta a) (Section 6.1); ``broyden`` and
-``rigid_broyden`` take those steps (inverse "good" Broyden update, full steps).
+``rigid_broyden`` take those steps (inverse "good" Broyden update, full steps). ``rigid_broyden``
+can also start from the Jacobian of each body's own free-space FCM mobility (not in the paper).
 
 Scaling used by ``rigid_broyden`` (a reading: the paper gives neither the norm nor
 the scaling): the unknowns are x = (F, W/mu) and the residual is
@@ -31,6 +32,7 @@ import math
 
 import numpy as np
 
+from . import closed_forms as cf
 from .grid_fcm import _as3, fast_fcm_apply
 
 
@@ -118,11 +120,31 @@ def broyden(residual, precond, x0, tol_abs, max_iter):
     return x, max_iter, norms
 
 
-def rigid_broyden(apply_vf, Y, body_off, X, L, ft, tol, max_iter, a=1.0, eta=1.0, x0=None):
-    """The rigid-body mobility problem by ``broyden`` with the diagonal-mobility Jacobian.
+def body_mobility(Yb, L, a=1.0, eta=1.0):
+    """The free-space FCM force-velocity mobility of one body's particles (3k x 3k): pair blocks
+    S(x; sigma sqrt 2) (eq. M_VF) for the minimum-image separations, 1/(6 pi eta a) I on the diagonal."""
+    L = _as3(L)
+    k = Yb.shape[0]
+    Mb = np.zeros((3 * k, 3 * k))
+    for i in range(k):
+        for j in range(k):
+            if i == j:
+                Mb[3 * i:3 * i + 3, 3 * j:3 * j + 3] = np.eye(3) / (6.0 * math.pi * eta * a)
+            else:
+                d = Yb[i] - Yb[j]
+                d = d - L * np.round(d / L)
+                Mb[3 * i:3 * i + 3, 3 * j:3 * j + 3] = cf.fcm_pair_mobility(d[None, :], a, eta)[0][0]
+    return Mb
+
+
+def rigid_broyden(apply_vf, Y, body_off, X, L, ft, tol, max_iter, a=1.0, eta=1.0, x0=None, precond="diagonal"):
+    """The rigid-body mobility problem by ``broyden``.
 
     ``apply_vf(F)`` returns V = M^VF F for F of shape (N, 3). Returns (F, W, iterations,
-    relative residual norms), W rows (U_b, Gamma_b).
+    relative residual norms), W rows (U_b, Gamma_b). precond: "diagonal" starts from the Jacobian
+    of the diagonal mobility mu I (the paper's choice); "body" from the Jacobian of the
+    block-diagonal mobility that keeps each body's own free-space FCM interactions
+    (``body_mobility``) and drops those between bodies, J0 = [[M_bb / mu, -K], [K^T, 0]] per body.
     """
     r = lever_arms(Y, body_off, X, L)
     n = r.shape[0]
@@ -155,7 +177,27 @@ def rigid_broyden(apply_vf, Y, body_off, X, L, ft, tol, max_iter, a=1.0, eta=1.0
             R2[b, 3:] = np.cross(rb, F[sl]).sum(axis=0) - ft[b, 3:]
         return np.concatenate([R1.ravel(), R2.ravel()])
 
-    def precond(v):
+    if precond == "body":
+        blocks = []
+        for b in range(nb):
+            sl = slice(body_off[b], body_off[b + 1])
+            Kb = constraint_matrix(Y[sl], np.array([0, body_off[b + 1] - body_off[b]]), X[b:b + 1], L)
+            Ab = np.block([[body_mobility(Y[sl], L, a, eta) / mu, -Kb], [Kb.T, np.zeros((6, 6))]])
+            blocks.append(np.linalg.inv(Ab))
+
+    def precond_body(v):
+        r1 = v[:3 * n].reshape(n, 3)
+        r2 = v[3 * n:].reshape(nb, 6)
+        F = np.empty((n, 3))
+        What = np.empty((nb, 6))
+        for b in range(nb):
+            sl = slice(body_off[b], body_off[b + 1])
+            sol = blocks[b] @ np.concatenate([r1[sl].ravel(), r2[b]])
+            F[sl] = sol[:-6].reshape(-1, 3)
+            What[b] = sol[-6:]
+        return np.concatenate([F.ravel(), What.ravel()])
+
+    def precond_diag(v):
         # J0^-1 (r1, r2): W = (K^T K)^-1 (r2 - K^T r1), F = r1 + K W
         r1 = v[:3 * n].reshape(n, 3)
         r2 = v[3 * n:].reshape(nb, 6)
@@ -172,15 +214,16 @@ def rigid_broyden(apply_vf, Y, body_off, X, L, ft, tol, max_iter, a=1.0, eta=1.0
     scale = float(np.linalg.norm(ft))
     if x0 is None:
         x0 = np.zeros(3 * n + 6 * nb)
-    x, it, norms = broyden(residual, precond, x0, tol * scale, max_iter)
+    x, it, norms = broyden(residual, precond_body if precond == "body" else precond_diag, x0, tol * scale, max_iter)
     F = x[:3 * n].reshape(n, 3)
     W = mu * x[3 * n:].reshape(nb, 6)
     rel = [v / scale for v in norms] if scale > 0 else norms
     return F, W, it, rel
 
 
-def fast_fcm_rigid_broyden(Y, body_off, X, ft, L, M, M_G, Sigma, R_c, tol, max_iter, a=1.0, eta=1.0):
+def fast_fcm_rigid_broyden(Y, body_off, X, ft, L, M, M_G, Sigma, R_c, tol, max_iter, a=1.0, eta=1.0,
+                           precond="diagonal"):
     """``rigid_broyden`` with the fast-FCM oracle product (forces only) as M^VF."""
     def apply_vf(F):
         return fast_fcm_apply(Y, F, None, L, M, M_G, Sigma, R_c, a=a, eta=eta)[0]
-    return rigid_broyden(apply_vf, Y, body_off, X, L, ft, tol, max_iter, a=a, eta=eta)
+    return rigid_broyden(apply_vf, Y, body_off, X, L, ft, tol, max_iter, a=a, eta=eta, precond=precond)

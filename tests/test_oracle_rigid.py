@@ -157,3 +157,37 @@ def test_rod_pushed_along_its_axis_translates_without_rotating():
     assert np.abs(Wpar[0, 1:]).max() < 1e-4 * abs(Wpar[0, 0])
     assert abs(Wperp[0, 0]) < 1e-4 * abs(Wperp[0, 1]) and np.abs(Wperp[0, 3:]).max() < 1e-4 * abs(Wperp[0, 1])
     assert Wpar[0, 0] > Wperp[0, 1] > 0.0
+
+
+def test_body_preconditioner_is_exact_for_isolated_bodies():
+    """With the mobility of bodies that do not interact (each body's own free-space FCM block), the
+    body preconditioner is the exact inverse Jacobian: Broyden ends after one step, at the dense
+    solution. The blocks themselves are the free-space FCM pair mobility (checked against S(x; sigma
+    sqrt 2) of the closed forms and symmetric)."""
+    from oracle import closed_forms as cf
+    L = np.array([80.0, 80.0, 40.0])
+    pos, off, X = inputs.doublet_rods(4, L[0], L[2], inputs.BASE_SEED + 105, lattice=False)
+    ft = inputs.rod_loads(4, inputs.BASE_SEED + 106, scale=1.0)
+    n = pos.shape[0]
+    Mbd = np.zeros((3 * n, 3 * n))
+    for b in range(4):
+        sl = slice(3 * off[b], 3 * off[b + 1])
+        Mbd[sl, sl] = orr.body_mobility(pos[off[b]:off[b + 1]], L)
+    assert np.allclose(Mbd, Mbd.T, rtol=0, atol=1e-15)
+    d = pos[1] - pos[0]
+    assert np.allclose(Mbd[0:3, 3:6], cf.S(d[None, :], cf.fcm_sigma() * math.sqrt(2.0))[0], rtol=1e-14, atol=0)
+    F0, W0 = orr.solve_saddle(Mbd, orr.constraint_matrix(pos, off, X, L), ft)
+    F, W, it, rel = orr.rigid_broyden(lambda f: (Mbd @ f.ravel()).reshape(-1, 3), pos, off, X, L, ft, 1e-12, 10,
+                                      precond="body")
+    assert it == 1 and rel[-1] < 1e-12
+    assert np.allclose(W, W0, rtol=1e-10, atol=0) and np.allclose(F, F0, rtol=1e-9, atol=1e-12)
+
+
+def test_body_preconditioner_converges_to_the_same_solution(fcm_system):
+    pos, off, X, MG, rc, Mvf, ft = fcm_system
+    F0, W0 = orr.solve_saddle(Mvf, orr.constraint_matrix(pos, off, X, L3), ft)
+    av = lambda f: (Mvf @ f.ravel()).reshape(-1, 3)
+    F, W, itb, rel = orr.rigid_broyden(av, pos, off, X, L3, ft, 1e-11, 200, precond="body")
+    _, _, itd, _ = orr.rigid_broyden(av, pos, off, X, L3, ft, 1e-11, 200)
+    assert rel[-1] <= 1e-11 and itb < itd
+    assert np.abs(W - W0).max() < 1e-9 * np.abs(W0).max()
