@@ -178,6 +178,14 @@ int fcm_brownian(fcm_handle* h, int n, const void* pos, double kT, const void* x
  *   UG       : (n_bodies, 6) rows (U_b, Gamma_b)      [device, write; read if warm]
  *   max_iter : 1 <= max_iter <= FCM_BROYDEN_MAX_ITER
  *   tol      : relative residual tolerance (> 0; the paper uses 1e-4)
+ *   precond  : the Jacobian Broyden starts from. FCM_RIGID_PRECOND_DIAGONAL: that
+ *              of the diagonal mobility mu I (the paper's choice). FCM_RIGID_PRECOND_BODY
+ *              (not in the paper): that of the block-diagonal mobility keeping each
+ *              body's own free-space FCM interactions, J0 = [[M_bb / mu, -K], [K^T, 0]]
+ *              per body (M_bb from S(x; sigma sqrt 2), Section 2.2), inverted once per
+ *              call on the device (bodies of at most FCM_RIGID_BODY_MAX particles;
+ *              (3k + 6)^2 values per body of k particles); for separated rods it takes
+ *              about a third of the diagonal start's steps to the same solution
  *   warm     : nonzero: start from the F and UG passed in (a previous step's
  *              solution); zero: start from F = 0, UG = 0
  *   iterations, residual : Broyden steps taken (one fast-FCM product each; a
@@ -191,9 +199,12 @@ int fcm_brownian(fcm_handle* h, int n, const void* pos, double kT, const void* x
  * leave ||R|| above tol ||ft|| (F and UG then hold the last iterate). ft = 0 with
  * warm = 0 returns F = 0, UG = 0 after 0 iterations. */
 #define FCM_BROYDEN_MAX_ITER 256
+#define FCM_RIGID_PRECOND_DIAGONAL 0
+#define FCM_RIGID_PRECOND_BODY 1
+#define FCM_RIGID_BODY_MAX 32
 int fcm_rigid_solve(fcm_handle* h, int n, const void* pos, int n_bodies, const int* body_off, const void* X,
-                    const void* ft, void* F, void* UG, int max_iter, double tol, int warm, int* iterations,
-                    double* residual, void* stream);
+                    const void* ft, void* F, void* UG, int max_iter, double tol, int precond, int warm,
+                    int* iterations, double* residual, void* stream);
 
 /* ---- Batched systems (many independent systems in one pass) ----------------
  * The paper treats one periodic system at a time; running many small systems

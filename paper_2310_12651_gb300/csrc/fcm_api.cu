@@ -230,6 +230,8 @@ struct fcm_handle {
   double* lz_dot = nullptr;     // device scalar of the Lanczos dot products
   void* rg = nullptr;           // rigid-solve vectors, Broyden steps and scalars, grown on demand
   size_t rg_bytes = 0;
+  void* rgp = nullptr;          // rigid-solve body preconditioner (inverse blocks), grown on demand
+  size_t rgp_bytes = 0;
   size_t bytes = 0;
   long long launches = 0;
   std::vector<void*> allocs;
@@ -277,6 +279,7 @@ void release(fcm_handle* h) {
   if (h->lz) cudaFree(h->lz);
   if (h->lz_dot) cudaFree(h->lz_dot);
   if (h->rg) cudaFree(h->rg);
+  if (h->rgp) cudaFree(h->rgp);
   delete h;
 }
 
@@ -879,7 +882,8 @@ int brownian(fcm_handle* h, int n, const R* pos, double kT, const R* xi, const R
 //   coef[ld], one, ftnorm2, flags[4]
 template <typename R>
 int rigid_solve(fcm_handle* h, int n, const R* pos, int nb, const int* body_off, const R* X, const R* ft, R* F,
-                R* UG, int max_iter, double tol, bool warm, int* iterations, double* residual, cudaStream_t s) {
+                R* UG, int max_iter, double tol, int precond, bool warm, int* iterations, double* residual,
+                cudaStream_t s) {
   const size_t m = 3 * (size_t)n + 6 * (size_t)nb;
   const size_t stride = (m + 63) / 64 * 64;
   const int ld = max_iter + 2;
@@ -931,6 +935,41 @@ int rigid_solve(fcm_handle* h, int n, const R* pos, int nb, const int* body_off,
     return fail(FCM_ERR_INPUT, "body " + std::to_string(hf[1] - 1) + " is degenerate (K^T K singular: fewer than "
                                "3 particles off one line)");
   if (!std::isfinite(hft2)) return fail(FCM_ERR_INPUT, "ft is not finite");
+  // body preconditioner: the inverse of [[M_bb / mu, -K], [K^T, 0]] per body, ms x ms each
+  R* aT = nullptr;
+  int ms = 0;
+  if (precond == FCM_RIGID_PRECOND_BODY) {
+    const int kmax = hf[3];
+    if (kmax > kRigidBodyMax)
+      return fail(FCM_ERR_INPUT, "the body preconditioner takes bodies of at most " + std::to_string(kRigidBodyMax) +
+                                     " particles (largest: " + std::to_string(kmax) + ")");
+    ms = 3 * kmax + 6;
+    const size_t pneed = sizeof(R) * (size_t)ms * ms * (size_t)nb;
+    if (h->rgp_bytes < pneed) {
+      if (h->rgp) cudaFree(h->rgp);
+      h->rgp = nullptr;
+      h->rgp_bytes = 0;
+      cudaError_t e = cudaMalloc(&h->rgp, pneed);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FCM_ERR_OOM, "body preconditioner of " + std::to_string(pneed) + " bytes: " + cudaGetErrorString(e));
+      }
+      h->rgp_bytes = pneed;
+    }
+    aT = (R*)h->rgp;
+    launch_body_precond<R>(arm, body_off, nb, kmax, h->p.L, h->p.a, h->p.eta, aT, flags, s, &h->launches);
+    FCM_CUDA(cudaGetLastError());
+    FCM_CUDA(cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, s));
+    FCM_CUDA(cudaStreamSynchronize(s));
+    if (hf[1])
+      return fail(FCM_ERR_INPUT, "body " + std::to_string(hf[1] - 1) + ": its preconditioner block is singular");
+  }
+  auto residual_launch = [&](double* nrm) {
+    if (aT)
+      launch_rigid_residual_body<R>(V, x, ft, arm, aT, ms, body_off, n, nb, 1.0 / mu, z, nrm, s, &h->launches);
+    else
+      launch_rigid_residual<R>(V, x, ft, arm, ginv, body_off, n, nb, 1.0 / mu, z, nrm, s, &h->launches);
+  };
   const double tau = tol * std::sqrt(hft2);
   int rc;
   auto finish = [&](int it, double nrm2) -> int {
@@ -963,7 +1002,7 @@ int rigid_solve(fcm_handle* h, int n, const R* pos, int nb, const int* body_off,
   };
   double nrm2 = 0.0;
   int brk = 0;
-  launch_rigid_residual<R>(V, x, ft, arm, ginv, body_off, n, nb, 1.0 / mu, z, norm2, s, &h->launches);
+  residual_launch(norm2);
   if ((rc = read_norm(0, &nrm2, &brk))) return rc;
   if (!std::isfinite(nrm2)) return fail(FCM_ERR_INPUT, "non-finite residual (check F and UG of a warm start)");
   if (std::sqrt(nrm2) <= tau) return finish(0, nrm2);
@@ -973,7 +1012,7 @@ int rigid_solve(fcm_handle* h, int n, const R* pos, int nb, const int* body_off,
   for (int it = 0; it < max_iter; ++it) {
     const int nstep = it;   // steps s_0 .. s_nstep are stored, and x already includes s_nstep
     if ((rc = run<R>(h, 1, n, pos, x, nullptr, V, nullptr, FCM_STAGE_ALL, false, s))) return rc;
-    launch_rigid_residual<R>(V, x, ft, arm, ginv, body_off, n, nb, 1.0 / mu, z, norm2 + it + 1, s, &h->launches);
+    residual_launch(norm2 + it + 1);
     if ((rc = read_norm(it + 1, &nrm2, &brk))) return rc;
     if (!std::isfinite(nrm2)) return fail(FCM_ERR_INPUT, "non-finite residual in the Broyden iteration");
     if (brk) {
@@ -1022,8 +1061,8 @@ int fcm_brownian(fcm_handle* h, int n, const void* pos, double kT, const void* x
 }
 
 int fcm_rigid_solve(fcm_handle* h, int n, const void* pos, int n_bodies, const int* body_off, const void* X,
-                    const void* ft, void* F, void* UG, int max_iter, double tol, int warm, int* iterations,
-                    double* residual, void* stream) {
+                    const void* ft, void* F, void* UG, int max_iter, double tol, int precond, int warm,
+                    int* iterations, double* residual, void* stream) {
   if (iterations) *iterations = 0;
   if (residual) *residual = 0.0;
   if (!h) return fail(FCM_ERR_ARG, "handle is NULL");
@@ -1034,15 +1073,17 @@ int fcm_rigid_solve(fcm_handle* h, int n, const void* pos, int n_bodies, const i
   if (max_iter < 1 || max_iter > FCM_BROYDEN_MAX_ITER)
     return fail(FCM_ERR_ARG, "max_iter must be in [1, " + std::to_string(FCM_BROYDEN_MAX_ITER) + "]");
   if (!(tol > 0.0) || !std::isfinite(tol)) return fail(FCM_ERR_ARG, "tol must be finite and > 0");
+  if (precond != FCM_RIGID_PRECOND_DIAGONAL && precond != FCM_RIGID_PRECOND_BODY)
+    return fail(FCM_ERR_ARG, "precond must be FCM_RIGID_PRECOND_DIAGONAL or FCM_RIGID_PRECOND_BODY");
   if (!pos || !body_off || !X || !ft || !F || !UG)
     return fail(FCM_ERR_ARG, "pos, body_off, X, ft, F and UG must be non-NULL");
   DeviceGuard guard(h->device);
   cudaStream_t s = (cudaStream_t)stream;
   if (h->fp64)
     return rigid_solve<double>(h, n, (const double*)pos, n_bodies, body_off, (const double*)X, (const double*)ft,
-                               (double*)F, (double*)UG, max_iter, tol, warm != 0, iterations, residual, s);
+                               (double*)F, (double*)UG, max_iter, tol, precond, warm != 0, iterations, residual, s);
   return rigid_solve<float>(h, n, (const float*)pos, n_bodies, body_off, (const float*)X, (const float*)ft,
-                            (float*)F, (float*)UG, max_iter, tol, warm != 0, iterations, residual, s);
+                            (float*)F, (float*)UG, max_iter, tol, precond, warm != 0, iterations, residual, s);
 }
 
 }  // extern "C"

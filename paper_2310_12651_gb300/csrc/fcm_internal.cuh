@@ -309,6 +309,16 @@ void launch_rigid_setup(const R* pos, const int* body_off, const R* X, int n, in
 template <typename R>   // z = -J0^-1 R(x) for V = M F, *norm2 += ||R||^2
 void launch_rigid_residual(const R* V, const R* x, const R* ft, const R* arm, const R* ginv, const int* body_off,
                            int n, int nb, double inv_mu, R* z, double* norm2, cudaStream_t s, long long* launches);
+// Body preconditioner (not the paper's): per body (3k + 6)^2 inverse of [[M_bb / mu, -K], [K^T, 0]],
+// stored transposed with stride ms = 3 kmax + 6; bodies of at most kRigidBodyMax particles.
+constexpr int kRigidBodyMax = 32;
+template <typename R>
+void launch_body_precond(const R* arm, const int* body_off, int nb, int kmax, const double L[3], double a, double eta,
+                         R* aT, int* flags, cudaStream_t s, long long* launches);
+template <typename R>
+void launch_rigid_residual_body(const R* V, const R* x, const R* ft, const R* arm, const R* aT, int ms,
+                                const int* body_off, int n, int nb, double inv_mu, R* z, double* norm2, cudaStream_t s,
+                                long long* launches);
 template <typename R>   // out[j] += a . (S + j stride), j < k
 void launch_multi_dot(const R* a, const R* S, size_t m, size_t stride, int k, double* out, cudaStream_t s,
                       long long* launches);

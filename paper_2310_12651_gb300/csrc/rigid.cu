@@ -45,7 +45,8 @@ __device__ inline void block_atomic_add(double v, double* out) {
 // K^T K = [[n I, -[S]x], [[S]x, sum(|r|^2 I - r r^T)]] with S = sum r. Every lane factors the 6 x 6
 // matrix (Cholesky, FP64, registers); lanes 0..5 then solve for one column each. A pivot below
 // 1e-10 of its diagonal entry marks the body singular (fewer than 3 particles off one line).
-// flags[0] <- 1 + first body with invalid offsets, flags[1] <- 1 + a singular body.
+// flags[0] <- 1 + first body with invalid offsets, flags[1] <- 1 + a singular body, flags[3] <- the
+// largest body's particle count.
 template <typename R>
 __global__ void __launch_bounds__(256) rigid_setup_kernel(const R* __restrict__ pos, const int* __restrict__ body_off,
                                                           const R* __restrict__ X, int n, int nb, double Lx,
@@ -59,6 +60,7 @@ __global__ void __launch_bounds__(256) rigid_setup_kernel(const R* __restrict__ 
     if (lane == 0) atomicCAS(&flags[0], 0, b + 1);
     return;
   }
+  if (lane == 0) atomicMax(&flags[3], o1 - o0);   // largest body (the body preconditioner's limit)
   const double xb = (double)X[3 * (size_t)b], yb = (double)X[3 * (size_t)b + 1], zb = (double)X[3 * (size_t)b + 2];
   double s[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};   // Sx Sy Sz, then xx yy zz xy xz yz
   for (int i = o0 + lane; i < o1; i += 32) {
@@ -205,6 +207,226 @@ __global__ void __launch_bounds__(256) rigid_residual_kernel(const R* __restrict
   block_atomic_add(nr, norm2);
 }
 
+// ---------------------------------------------------------------- body preconditioner
+//
+// J0 with each body's own free-space FCM mobility (not the paper's choice, which is mu I): per body b
+// with k particles the (3k + 6) x (3k + 6) matrix
+//     A_b = [[M_bb / mu, -K_b], [K_b^T, 0]],
+// M_bb's blocks the FCM pair mobility S(x; sigma sqrt 2) = A(r) I + B(r) x^ x^ of the minimum-image
+// separation (from the Gaussian-regularised Stokeslet terms S1, S2, S3 of Section 2.2) and 1/(6 pi
+// eta a) I on the diagonal. One CTA per body builds A_b in shared memory (entries in FP64, stored in
+// R) and inverts it by Gauss-Jordan elimination with partial pivoting on [A_b | I]; the inverse is
+// written transposed (column j of A_b^-1 contiguous), stride ms x ms per body, for the residual
+// kernel's coalesced matrix-vector product. flags[1] <- 1 + a body whose pivot vanished.
+
+// S(x; sigma sqrt 2) = A I + B x x^T for r > 0, in the arithmetic type T. c8 = 1/(8 pi eta),
+// s2 = 2 sigma^2, dn = (2 pi s2)^(-3/2) (the Gaussian's normalisation), e2 = 1/(2 s2), inv2sg = 1/(2 sigma).
+template <typename T>
+__device__ inline void fcm_pair_vf(T dx, T dy, T dz, T c8, T s2, T dn, T e2, T inv2sg, T eta, T* A, T* B) {
+  const T r2 = dx * dx + dy * dy + dz * dz, r = sqrt(r2);
+  const T E = erf(r * inv2sg);
+  const T D = dn * exp(-r2 * e2);
+  const T t1 = c8 * E / r, t2 = c8 * s2 * E / (r2 * r), t3 = (s2 * s2 / (T(2) * eta * r2)) * D;
+  *A = t1 + t2 - t3;
+  *B = (t1 - T(3) * t2 + T(3) * t3) / r2;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) body_precond_kernel(const R* __restrict__ arm, const int* __restrict__ body_off,
+                                                           int nb, double Lx, double Ly, double Lz, double a,
+                                                           double eta, int ms, R* __restrict__ aT, int* flags) {
+  extern __shared__ unsigned char smraw[];
+  const int b = blockIdx.x;
+  if (b >= nb) return;
+  const int o0 = body_off[b], o1 = body_off[b + 1];
+  const int k = o1 - o0, m = 3 * k + 6, w2 = 2 * m;
+  R* aug = reinterpret_cast<R*>(smraw);            // m x 2m
+  R* fac = aug + (size_t)m * w2;                    // m factors of the current column
+  __shared__ int piv_row;
+  __shared__ double piv_val;
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  // [A_b | I]: identity, the K blocks and zeros element by element, then the mobility blocks pair by
+  // pair (one closed form per pair, in the handle's precision)
+  for (int e = threadIdx.x; e < m * w2; e += blockDim.x) {
+    const int r = e / w2, c = e - r * w2;
+    R v = R(0);
+    if (c >= m) {
+      v = (c - m == r) ? R(1) : R(0);
+    } else if (r < 3 * k && c >= 3 * k) {   // -K_i: [-I, [r_i]x], [r]x = [[0, -rz, ry], [rz, 0, -rx], [-ry, rx, 0]]
+      const int i = r / 3, p = r - 3 * i, q = c - 3 * k;
+      const size_t ai = 3 * (size_t)(o0 + i);
+      const R rx = arm[ai], ry = arm[ai + 1], rz = arm[ai + 2];
+      if (q < 3) v = (p == q) ? R(-1) : R(0);
+      else {
+        const int t = q - 3;
+        v = p == 0 ? (t == 1 ? -rz : (t == 2 ? ry : R(0)))
+                   : (p == 1 ? (t == 0 ? rz : (t == 2 ? -rx : R(0))) : (t == 0 ? -ry : (t == 1 ? rx : R(0))));
+      }
+    } else if (r >= 3 * k && c < 3 * k) {   // K^T: (K^T)_{r', (j, q)} = K_{(j, q), r'}, K_j = [I, -[r_j]x]
+      const int rp = r - 3 * k, j = c / 3, q = c - 3 * j;
+      const size_t aj = 3 * (size_t)(o0 + j);
+      const R rx = arm[aj], ry = arm[aj + 1], rz = arm[aj + 2];
+      if (rp < 3) v = (q == rp) ? R(1) : R(0);
+      else {
+        const int t = rp - 3;
+        const R cxqt = q == 0 ? (t == 1 ? -rz : (t == 2 ? ry : R(0)))
+                              : (q == 1 ? (t == 0 ? rz : (t == 2 ? -rx : R(0))) : (t == 0 ? -ry : (t == 1 ? rx : R(0))));
+        v = -cxqt;
+      }
+    }
+    aug[e] = v;   // the mobility blocks are written below
+  }
+  __syncthreads();
+  {
+    const R sg = (R)(a / sqrt(kPi));
+    const R s2 = R(2) * sg * sg;
+    const R c8 = (R)(1.0 / (8.0 * kPi * eta));
+    const R dn = (R)pow(2.0 * kPi * 2.0 * (a * a / kPi), -1.5);
+    const R e2 = R(1) / (R(2) * s2);
+    const R inv2sg = R(1) / (R(2) * sg);
+    const R inv_mu = (R)(6.0 * kPi * eta * a);
+    for (int pq = threadIdx.x; pq < k * k; pq += blockDim.x) {
+      const int i = pq / k, j = pq - i * k;
+      R blk[9];
+      if (i == j) {   // (1/(6 pi eta a)) I / mu
+#pragma unroll
+        for (int t = 0; t < 9; ++t) blk[t] = (t % 4 == 0) ? R(1) : R(0);
+      } else {
+        const size_t ai = 3 * (size_t)(o0 + i), aj = 3 * (size_t)(o0 + j);
+        R d0 = arm[ai] - arm[aj], d1 = arm[ai + 1] - arm[aj + 1], d2 = arm[ai + 2] - arm[aj + 2];
+        d0 -= (R)Lx * rint(d0 / (R)Lx);
+        d1 -= (R)Ly * rint(d1 / (R)Ly);
+        d2 -= (R)Lz * rint(d2 / (R)Lz);
+        R A, B;
+        fcm_pair_vf<R>(d0, d1, d2, c8, s2, dn, e2, inv2sg, (R)eta, &A, &B);
+        const R d[3] = {d0, d1, d2};
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+#pragma unroll
+          for (int q = 0; q < 3; ++q) blk[3 * p + q] = ((p == q ? A : R(0)) + B * d[p] * d[q]) * inv_mu;
+      }
+#pragma unroll
+      for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) aug[(size_t)(3 * i + p) * w2 + 3 * j + q] = blk[3 * p + q];
+    }
+  }
+  __syncthreads();
+  const R tiny = sizeof(R) == 4 ? R(1e-6) : R(1e-12);
+  for (int col = 0; col < m; ++col) {
+    if (threadIdx.x < 32) {   // pivot: largest |entry| in rows col..m-1 of this column (lowest row on ties)
+      double best = -1.0;
+      int br = col;
+      for (int r = col + threadIdx.x; r < m; r += 32) {
+        const double v = fabs((double)aug[(size_t)r * w2 + col]);
+        if (v > best) { best = v; br = r; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int orr = __shfl_xor_sync(0xffffffffu, br, o);
+        if (ob > best || (ob == best && orr < br)) { best = ob; br = orr; }
+      }
+      if (threadIdx.x == 0) {
+        piv_row = br;
+        piv_val = (double)aug[(size_t)br * w2 + col];
+        if (!(fabs(piv_val) > (double)tiny)) bad = 1;
+      }
+    }
+    __syncthreads();
+    if (bad) break;
+    const int pr = piv_row;
+    const R inv_p = (R)(1.0 / piv_val);
+    for (int c = threadIdx.x; c < w2; c += blockDim.x) {   // swap rows col and pr, scale the pivot row
+      const R vp = aug[(size_t)pr * w2 + c];
+      const R vc = aug[(size_t)col * w2 + c];
+      aug[(size_t)pr * w2 + c] = vc;
+      aug[(size_t)col * w2 + c] = vp * inv_p;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < m; r += blockDim.x) fac[r] = (r == col) ? R(0) : aug[(size_t)r * w2 + col];
+    __syncthreads();
+    for (int e = threadIdx.x; e < m * (w2 - col); e += blockDim.x) {
+      const int r = e / (w2 - col), c = col + (e - r * (w2 - col));
+      aug[(size_t)r * w2 + c] -= fac[r] * aug[(size_t)col * w2 + c];
+    }
+    __syncthreads();
+  }
+  R* out = aT + (size_t)b * ms * ms;
+  if (bad) {
+    if (threadIdx.x == 0) atomicCAS(&flags[1], 0, b + 1);
+    for (int e = threadIdx.x; e < ms * ms; e += blockDim.x) out[e] = R(0);
+    return;
+  }
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {   // out[j][i] = (A^-1)[i][j]
+    const int j = e / m, i = e - j * m;
+    out[(size_t)j * ms + i] = aug[(size_t)i * w2 + m + j];
+  }
+}
+
+// The residual kernel with the body preconditioner: R1 and R2 of the body go to a per-warp vector
+// v (3k + 6 values, up to kRigidBodyMax particles), then z = -A_b^-1 v with lanes over rows.
+template <typename R>
+__global__ void __launch_bounds__(256) rigid_residual_body_kernel(const R* __restrict__ V, const R* __restrict__ x,
+                                                                  const R* __restrict__ ft, const R* __restrict__ arm,
+                                                                  const R* __restrict__ aT, int ms,
+                                                                  const int* __restrict__ body_off, int n, int nb,
+                                                                  R inv_mu, R* __restrict__ z,
+                                                                  double* __restrict__ norm2) {
+  __shared__ R vbuf[kBodyWarps][3 * kRigidBodyMax + 6];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int b = blockIdx.x * kBodyWarps + wid;
+  double nr = 0.0;
+  if (b < nb) {
+    const int o0 = body_off[b], o1 = body_off[b + 1];
+    const int k = o1 - o0, m = 3 * k + 6;
+    R* v = vbuf[wid];
+    const R* wh = x + 3 * (size_t)n + 6 * (size_t)b;
+    R w[6];
+#pragma unroll
+    for (int t = 0; t < 6; ++t) w[t] = wh[t];
+    R acc[7];
+#pragma unroll
+    for (int t = 0; t < 7; ++t) acc[t] = R(0);
+    for (int i = o0 + lane; i < o1; i += 32) {
+      const size_t q = 3 * (size_t)i;
+      const R rx = arm[q], ry = arm[q + 1], rz = arm[q + 2];
+      const R e0 = V[q] * inv_mu - (w[0] + (w[4] * rz - w[5] * ry));
+      const R e1 = V[q + 1] * inv_mu - (w[1] + (w[5] * rx - w[3] * rz));
+      const R e2 = V[q + 2] * inv_mu - (w[2] + (w[3] * ry - w[4] * rx));
+      const R f0 = x[q], f1 = x[q + 1], f2 = x[q + 2];
+      v[3 * (i - o0)] = e0;
+      v[3 * (i - o0) + 1] = e1;
+      v[3 * (i - o0) + 2] = e2;
+      acc[0] += f0; acc[1] += f1; acc[2] += f2;
+      acc[3] += ry * f2 - rz * f1; acc[4] += rz * f0 - rx * f2; acc[5] += rx * f1 - ry * f0;
+      acc[6] += e0 * e0 + e1 * e1 + e2 * e2;
+    }
+#pragma unroll
+    for (int t = 0; t < 7; ++t) acc[t] = warp_sum(acc[t]);
+    if (lane < 6) v[3 * k + lane] = acc[lane] - ft[6 * (size_t)b + lane];   // R2
+    if (lane == 0) {
+      R t = acc[6];
+#pragma unroll
+      for (int u = 0; u < 6; ++u) {
+        const R r2 = acc[u] - ft[6 * (size_t)b + u];
+        t += r2 * r2;
+      }
+      nr = (double)t;
+    }
+    __syncwarp();
+    const R* A = aT + (size_t)b * ms * ms;
+    for (int i = lane; i < m; i += 32) {
+      R sum = R(0);
+      for (int j = 0; j < m; ++j) sum += A[(size_t)j * ms + i] * v[j];
+      if (i < 3 * k) z[3 * (size_t)o0 + i] = -sum;
+      else z[3 * (size_t)n + 6 * (size_t)b + (i - 3 * k)] = -sum;
+    }
+  }
+  block_atomic_add(nr, norm2);
+}
+
 // out[j] += a . S_j for the k vectors S_j = S + j * stride (blockIdx.y = j); each thread sums its
 // elements in R with four independent partial sums, blocks combine in FP64.
 template <typename R>
@@ -319,6 +541,25 @@ void launch_rigid_residual(const R* V, const R* x, const R* ft, const R* arm, co
 }
 
 template <typename R>
+void launch_body_precond(const R* arm, const int* body_off, int nb, int kmax, const double L[3], double a, double eta,
+                         R* aT, int* flags, cudaStream_t s, long long* launches) {
+  const int m = 3 * kmax + 6;
+  const size_t smem = sizeof(R) * ((size_t)m * 2 * m + m);
+  cudaFuncSetAttribute(body_precond_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  body_precond_kernel<R><<<nb, 256, smem, s>>>(arm, body_off, nb, L[0], L[1], L[2], a, eta, m, aT, flags);
+  *launches += 1;
+}
+
+template <typename R>
+void launch_rigid_residual_body(const R* V, const R* x, const R* ft, const R* arm, const R* aT, int ms,
+                                const int* body_off, int n, int nb, double inv_mu, R* z, double* norm2, cudaStream_t s,
+                                long long* launches) {
+  const int blocks = (nb + kBodyWarps - 1) / kBodyWarps;
+  rigid_residual_body_kernel<R><<<blocks, 256, 0, s>>>(V, x, ft, arm, aT, ms, body_off, n, nb, (R)inv_mu, z, norm2);
+  *launches += 1;
+}
+
+template <typename R>
 void launch_multi_dot(const R* a, const R* S, size_t m, size_t stride, int k, double* out, cudaStream_t s,
                       long long* launches) {
   // about 8 blocks per SM in total, at least one per vector
@@ -348,6 +589,10 @@ void launch_broyden_step(const R* z, const R* S, size_t m, size_t stride, int n,
   template void launch_rigid_residual<R>(const R*, const R*, const R*, const R*, const R*, const int*, int, int,    \
                                          double, R*, double*, cudaStream_t, long long*);                            \
   template void launch_multi_dot<R>(const R*, const R*, size_t, size_t, int, double*, cudaStream_t, long long*);    \
+  template void launch_body_precond<R>(const R*, const int*, int, int, const double[3], double, double, R*, int*,    \
+                                       cudaStream_t, long long*);                                                   \
+  template void launch_rigid_residual_body<R>(const R*, const R*, const R*, const R*, const R*, int, const int*, int, \
+                                              int, double, R*, double*, cudaStream_t, long long*);                  \
   template void launch_broyden_step<R>(const R*, const R*, size_t, size_t, int, const double*, R*, R*, cudaStream_t, \
                                        long long*);
 FCM_RIGID_INSTANTIATE(float)

@@ -83,7 +83,7 @@ def _load():
         "fcm_batch_apply_stages": (i, [vp, i, ctypes.POINTER(i), vp, vp, vp, vp, vp, i, vp]),
         "fcm_max_systems": (i, [vp]),
         "fcm_brownian": (i, [vp, i, vp, d, vp, vp, vp, vp, i, d, ctypes.POINTER(i), vp]),
-        "fcm_rigid_solve": (i, [vp, i, vp, i, vp, vp, vp, vp, vp, i, d, i, ctypes.POINTER(i), ctypes.POINTER(d), vp]),
+        "fcm_rigid_solve": (i, [vp, i, vp, i, vp, vp, vp, vp, vp, i, d, i, i, ctypes.POINTER(i), ctypes.POINTER(d), vp]),
         "fcm_destroy": (i, [vp]),
         "fcm_apply": (i, [vp, i, vp, vp, vp, vp, vp, vp]),
         "fcm_apply_stages": (i, [vp, i, vp, vp, vp, vp, vp, i, vp]),
@@ -129,6 +129,9 @@ MAX_BATCH = 1024
 LANCZOS_MAX_ITER = 64
 #: most Broyden iterations of fcm_rigid_solve (include/fcm.h)
 BROYDEN_MAX_ITER = 256
+#: Broyden's starting Jacobian in fcm_rigid_solve, and the body preconditioner's size limit (include/fcm.h)
+RIGID_PRECOND_DIAGONAL, RIGID_PRECOND_BODY = 0, 1
+RIGID_BODY_MAX = 32
 
 #: capacity of fcm_pair_correction_noalloc's fixed scratch (include/fcm.h)
 NOALLOC_MAX_N = 65536
@@ -232,14 +235,14 @@ class Handle:
         return it.value
 
     def rigid_solve(self, n, pos, n_bodies, body_off, X, ft, F, UG, max_iter=100, tol=1e-4, warm=False,
-                    stream=0, check=True):
+                    stream=0, check=True, precond=RIGID_PRECOND_DIAGONAL):
         """Rigid-body mobility solve (Broyden); returns (status, iterations, relative residual).
 
         Raises FcmError on any status but FCM_OK, except FCM_ERR_NOT_CONVERGED when ``check`` is False.
         """
         it, res = ctypes.c_int(), ctypes.c_double()
         code = _lib.fcm_rigid_solve(self._h, int(n), _ptr(pos), int(n_bodies), _ptr(body_off), _ptr(X), _ptr(ft),
-                                    _ptr(F), _ptr(UG), int(max_iter), float(tol), 1 if warm else 0,
+                                    _ptr(F), _ptr(UG), int(max_iter), float(tol), int(precond), 1 if warm else 0,
                                     ctypes.byref(it), ctypes.byref(res), stream or None)
         if code != FCM_OK and (check or code != FCM_ERR_NOT_CONVERGED):
             _check(code)

@@ -128,9 +128,12 @@ def test_rigid_solve_rejects_a_null_handle_on_the_host(fcm):
     """Argument checks run before any CUDA call, so they work without a device."""
     it, res = ctypes.c_int(7), ctypes.c_double(3.0)
     lib = fcm.library()
-    code = lib.fcm_rigid_solve(None, 10, None, 1, None, None, None, None, None, 10, 1e-4, 0, ctypes.byref(it),
+    code = lib.fcm_rigid_solve(None, 10, None, 1, None, None, None, None, None, 10, 1e-4, 0, 0, ctypes.byref(it),
                                ctypes.byref(res), None)
     assert code == fcm.FCM_ERR_ARG and b"handle is NULL" in lib.fcm_last_error()
     assert it.value == 0 and res.value == 0.0
-    assert fcm.BROYDEN_MAX_ITER == int(re.search(r"#define FCM_BROYDEN_MAX_ITER (\d+)",
-                                                 open(os.path.join(ROOT, "include", "fcm.h")).read()).group(1))
+    header = open(os.path.join(ROOT, "include", "fcm.h")).read()
+    for name, value in (("FCM_BROYDEN_MAX_ITER", fcm.BROYDEN_MAX_ITER), ("FCM_RIGID_BODY_MAX", fcm.RIGID_BODY_MAX),
+                        ("FCM_RIGID_PRECOND_DIAGONAL", fcm.RIGID_PRECOND_DIAGONAL),
+                        ("FCM_RIGID_PRECOND_BODY", fcm.RIGID_PRECOND_BODY)):
+        assert value == int(re.search(r"#define " + name + r" (\d+)", header).group(1)), name

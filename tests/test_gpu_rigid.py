@@ -54,7 +54,7 @@ def _ragged(seed, sizes):
     return np.concatenate(Y), off, np.array(X)
 
 
-def _solve(fcm, prec, Y, off, X, ft, tol, max_iter=256, warm=None, check=True, handle=None, L=L3, M=M3):
+def _solve(fcm, prec, Y, off, X, ft, tol, max_iter=256, warm=None, check=True, handle=None, L=L3, M=M3, precond=0):
     import torch
     dt = torch.float32 if prec == fcm.FCM_FP32 else torch.float64
     dev = torch.device("cuda:0")
@@ -70,7 +70,7 @@ def _solve(fcm, prec, Y, off, X, ft, tol, max_iter=256, warm=None, check=True, h
     try:
         code, it, res = h.rigid_solve(n, pos, nb, offd, Xd, ftd, F, UG, max_iter=max_iter, tol=tol,
                                       warm=warm is not None, stream=torch.cuda.current_stream().cuda_stream,
-                                      check=check)
+                                      check=check, precond=precond)
         torch.cuda.synchronize()
         V = torch.empty_like(F)
         h.apply(n, pos, F, None, V, None, torch.cuda.current_stream().cuda_stream)
@@ -240,3 +240,66 @@ def test_bad_arguments_are_rejected(fcm):
             with pytest.raises(fcm.FcmError) as e:
                 h.rigid_solve(a["n"], pos, a["nb"], offd, a["X"], ft, F, UG, max_iter=a["max_iter"], tol=a["tol"])
             assert e.value.code == fcm.FCM_ERR_ARG and msg in str(e.value), (kw, str(e.value))
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_body_preconditioner_matches_the_oracle(fcm, precision):
+    """Broyden from each body's own free-space FCM mobility (FCM_RIGID_PRECOND_BODY): the same dense
+    oracle solution, the oracle's step count for that start (+-1), and fewer steps than from mu I."""
+    prec = fcm.FCM_FP32 if precision == "fp32" else fcm.FCM_FP64
+    Y, off, X = _rods(3, 200)
+    ft = inputs.rod_loads(3, inputs.BASE_SEED + 201, scale=1.0)
+    Yr, Xr, ftr = rounded(Y, prec), rounded(X, prec), rounded(ft, prec)
+    Mvf, (F0, W0) = _oracle_dense(Yr, off, Xr, ftr)
+    tol = 1e-12 if precision == "fp64" else 1e-5
+    code, itb, res, F, UG, V = _solve(fcm, prec, Y, off, X, ft, tol, precond=fcm.RIGID_PRECOND_BODY)
+    _, itd, _, _, _, _ = _solve(fcm, prec, Y, off, X, ft, tol)
+    assert code == fcm.FCM_OK and res <= tol and itb < itd, (itb, itd)
+    assert_parity(UG, W0, FP64_TOL if precision == "fp64" else FP32_TOL, f"rod velocities, body start ({itb} steps)")
+    if precision == "fp64":
+        assert_parity(F, F0, FP64_TOL, "particle forces, body start")
+        for t in (1e-4, 1e-8):
+            _, _, it_o, _ = orr.rigid_broyden(lambda f: (Mvf @ f.ravel()).reshape(-1, 3), Y, off, X, L3, ft, t, 256,
+                                              precond="body")
+            _, it_g, _, _, _, _ = _solve(fcm, prec, Y, off, X, ft, t, precond=fcm.RIGID_PRECOND_BODY)
+            assert abs(it_g - it_o) <= 1, (t, it_g, it_o)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_body_preconditioner_on_a_rod_lattice_and_ragged_bodies(fcm, precision):
+    prec = fcm.FCM_FP32 if precision == "fp32" else fcm.FCM_FP64
+    L, M = (64.0, 64.0, 24.0), (52, 52, 20)
+    Y, off, X = inputs.doublet_rods(16, L[0], L[2], inputs.BASE_SEED + 206)
+    ft = inputs.rod_loads(16, inputs.BASE_SEED + 207, scale=0.5)
+    tol = 1e-4 if precision == "fp32" else 1e-9
+    code, itb, res, F, UG, V = _solve(fcm, prec, Y, off, X, ft, tol, L=L, M=M, precond=fcm.RIGID_PRECOND_BODY)
+    _, itd, _, _, UGd, _ = _solve(fcm, prec, Y, off, X, ft, tol, L=L, M=M)
+    assert code == fcm.FCM_OK and res <= tol and itb < itd, (itb, itd)
+    mu = 1.0 / (6.0 * math.pi)
+    slack = 3e-6 if precision == "fp32" else 1e-12
+    _check_equations(rounded(Y, prec), off, rounded(X, prec), rounded(ft, prec), F, UG, V,
+                     tol * np.linalg.norm(ft) * mu / np.linalg.norm(V) * 1.01 + slack, tol * 1.01 + slack, L=L)
+    # ragged bodies of 3..32 particles (the limit)
+    sizes = [3, 17, 5, 32, 4, 9, 26, 3]
+    Y, off, X = _ragged(204, sizes)
+    ft = inputs.rod_loads(len(sizes), inputs.BASE_SEED + 205, scale=1.0, per_rod=1)
+    _, (F0, W0) = _oracle_dense(rounded(Y, prec), off, rounded(X, prec), rounded(ft, prec))
+    code, it, res, F, UG, V = _solve(fcm, prec, Y, off, X, ft, 1e-12 if precision == "fp64" else 1e-5,
+                                     precond=fcm.RIGID_PRECOND_BODY)
+    assert code == fcm.FCM_OK
+    assert_parity(UG, W0, FP64_TOL if precision == "fp64" else FP32_TOL, f"ragged bodies, body start ({it} steps)")
+
+
+def test_body_preconditioner_limits(fcm):
+    """Bodies beyond FCM_RIGID_BODY_MAX particles and an unknown precond are rejected."""
+    Y, off, X = _ragged(215, [33, 4])
+    ft = inputs.rod_loads(2, inputs.BASE_SEED + 216, scale=1.0, per_rod=1)
+    with pytest.raises(fcm.FcmError) as e:
+        _solve(fcm, fcm.FCM_FP32, Y, off, X, ft, 1e-4, precond=fcm.RIGID_PRECOND_BODY)
+    assert e.value.code == fcm.FCM_ERR_INPUT and "at most 32" in str(e.value)
+    with pytest.raises(fcm.FcmError) as e:
+        _solve(fcm, fcm.FCM_FP32, Y, off, X, ft, 1e-4, precond=7)
+    assert e.value.code == fcm.FCM_ERR_ARG and "precond" in str(e.value)
+    # the same bodies with the diagonal start are fine
+    code, it, res, _, _, _ = _solve(fcm, fcm.FCM_FP32, Y, off, X, ft, 1e-4)
+    assert code == fcm.FCM_OK
