@@ -113,7 +113,8 @@ def test_rod_suspension_rigid_solve_full_size(fcm):
     """fcm_rigid_solve on the 7,744-rod suspension in the launch configuration bench.py times
     (FP32, Broyden tol 1e-4): the equations it solves hold on the host (rigid particle velocities
     under fcm_apply, rod force and torque sums), and the rod velocities agree with an FP64 solve at
-    1e-8 on the same GPU (the FP64 solve is held to the dense oracle at small sizes)."""
+    1e-8 on the same GPU (the FP64 solve is held to the dense oracle at small sizes); the solve from
+    each rod's own mobility (body preconditioner) takes fewer steps to the same rod velocities."""
     import math
     import torch
     import bench
@@ -126,7 +127,10 @@ def test_rod_suspension_rigid_solve_full_size(fcm):
     dev = torch.device("cuda:0")
     st = torch.cuda.current_stream().cuda_stream
     out = {}
-    for prec, t in ((fcm.FCM_FP32, tol), (fcm.FCM_FP64, 1e-8)):
+    for prec, t, pc in ((fcm.FCM_FP32, tol, 0), (fcm.FCM_FP64, 1e-8, 0), ("body", tol, 1)):
+        pc = fcm.RIGID_PRECOND_BODY if pc else fcm.RIGID_PRECOND_DIAGONAL
+        key = prec
+        prec = fcm.FCM_FP32 if prec == "body" else prec
         dt = torch.float32 if prec == fcm.FCM_FP32 else torch.float64
         tens = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
         pos, Xd, ftd = tens(Y), tens(X), tens(ft)
@@ -135,13 +139,15 @@ def test_rod_suspension_rigid_solve_full_size(fcm):
         p = fcm.make_params((Lxy, Lxy, Lz), pr["M"], pr["Sigma"], pr["r_c"], pr["M_G"], n, prec)
         with fcm.Handle(p) as h:
             code, it, res = h.rigid_solve(n, pos, n_rods, torch.as_tensor(off, device=dev), Xd, ftd, F, UG,
-                                          max_iter=256, tol=t, stream=st)
+                                          max_iter=256, tol=t, stream=st, precond=pc)
             V = torch.empty_like(F)
             h.apply(n, pos, F, None, V, None, st)
             torch.cuda.synchronize()
-        assert code == fcm.FCM_OK and res <= t and it < 100, (prec, it, res)
-        out[prec] = (F.double().cpu().numpy(), UG.double().cpu().numpy(), V.double().cpu().numpy())
-    F, UG, V = out[fcm.FCM_FP32]
+        assert code == fcm.FCM_OK and res <= t and it < 100, (key, it, res)
+        out[key] = (F.double().cpu().numpy(), UG.double().cpu().numpy(), V.double().cpu().numpy(), it)
+    assert out["body"][3] < out[fcm.FCM_FP32][3]   # fewer steps from each rod's own mobility
+    assert rel_l2(out["body"][1], out[fcm.FCM_FP64][1]) <= 1e-4
+    F, UG, V, _ = out[fcm.FCM_FP32]
     Lv = np.array([Lxy, Lxy, Lz])
     r = rounded(Y, fcm.FCM_FP32).reshape(n_rods, 22, 3) - rounded(X, fcm.FCM_FP32)[:, None, :]
     r -= Lv * np.round(r / Lv)
