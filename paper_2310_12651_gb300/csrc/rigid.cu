@@ -347,9 +347,15 @@ __global__ void __launch_bounds__(256) body_precond_kernel(const R* __restrict__
     __syncthreads();
     for (int r = threadIdx.x; r < m; r += blockDim.x) fac[r] = (r == col) ? R(0) : aug[(size_t)r * w2 + col];
     __syncthreads();
-    for (int e = threadIdx.x; e < m * (w2 - col); e += blockDim.x) {
-      const int r = e / (w2 - col), c = col + (e - r * (w2 - col));
-      aug[(size_t)r * w2 + c] -= fac[r] * aug[(size_t)col * w2 + c];
+    {   // warps over rows, lanes over columns (no division per element)
+      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+      for (int r = wid; r < m; r += nw) {
+        const R f = fac[r];
+        if (f == R(0)) continue;
+        R* rowr = aug + (size_t)r * w2;
+        const R* rowc = aug + (size_t)col * w2;
+        for (int c = col + lane; c < w2; c += 32) rowr[c] -= f * rowc[c];
+      }
     }
     __syncthreads();
   }
