@@ -20,14 +20,24 @@
 
 namespace fcm {
 
+// Forces only: the row's weight at each point, w = GQ g + GB d^2 g, is formed once and scaled by the
+// three force components (5 operations per point); with torques the terms are kept per component.
 template <int OX, int MGT, int EXT, bool GUARD, bool TORQUE, bool SAMEW>
 __device__ __forceinline__ void add_row(const float4* __restrict__ xt, int MG, float (&sx)[EXT], float (&sy)[EXT],
                                         float (&sz)[EXT], float ax, float ay, float az, float bx, float by, float bz,
-                                        float cx, float cy, float cz, float ky, float kz) {
+                                        float cx, float cy, float cz, float ky, float kz, float gq, float gb,
+                                        float4 f) {
 #pragma unroll
   for (int j = 0; j < MGT; ++j) {
     if (!GUARD || j < MG) {
       const float4 xv = xt[j];
+      if (!TORQUE) {
+        const float w = fmaf(gb, xv.y, gq * xv.x);
+        sx[OX + j] = fmaf(f.x, w, sx[OX + j]);
+        sy[OX + j] = fmaf(f.y, w, sy[OX + j]);
+        sz[OX + j] = fmaf(f.z, w, sz[OX + j]);
+        continue;
+      }
       float vx = fmaf(bx, xv.y, fmaf(ax, xv.x, sx[OX + j]));
       float vy = fmaf(by, xv.y, fmaf(ay, xv.x, sy[OX + j]));
       float vz = fmaf(bz, xv.y, fmaf(az, xv.x, sz[OX + j]));
@@ -195,7 +205,8 @@ __global__ void __launch_bounds__(rows_threads(MGT), 1) spread_rows_kernel(Geome
       const float4* xt = tb.xt + q * MGT;
 #define FCM_ROW_CASE(OX)                                                                                     \
   case OX:                                                                                                   \
-    add_row<OX, MGT, EXT, GUARD, TORQUE, SAMEW>(xt, MG, sx, sy, sz, ax, ay, az, bx, by, bz, cx, cy, cz, ky, kz); \
+    add_row<OX, MGT, EXT, GUARD, TORQUE, SAMEW>(xt, MG, sx, sy, sz, ax, ay, az, bx, by, bz, cx, cy, cz, ky, kz, GQ, \
+                                                GB, f);                                                          \
     break;
       switch (off.x) {
         FCM_ROW_CASE(0) FCM_ROW_CASE(1) FCM_ROW_CASE(2) FCM_ROW_CASE(3)
