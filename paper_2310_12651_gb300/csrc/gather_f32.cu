@@ -72,6 +72,27 @@ __global__ void __launch_bounds__(256) gather_tile_kernel(Geometry<float> g, Ker
       const float gdy = SAMEW ? gy : __shfl_sync(kFullMask32, gdyl, sy);
       const float gdz = SAMEW ? gz : __shfl_sync(kFullMask32, gdzl, sz);
       if (!active) return;
+      if (!TORQUE) {   // forces only: one weight per point, w = GQ g + GB d^2 g, for the three components
+        const float G = kc.nrm * gy * gz;
+        const float GQ = G * fmaf(kc.B, fmaf(dy, dy, dz * dz), kc.A);
+        const float GB = G * kc.B;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll
+        for (int j = 0; j < MGT; ++j) {
+          if (!GUARD || j < MG) {
+            const float w = fmaf(GB, gx2[j], GQ * gx[j]);
+            const float ux = row[j];
+            const float2 uyz = reinterpret_cast<const float2*>(acc + yz_plane_offset(l))[(row - acc) + j];
+            a0 = fmaf(w, ux, a0);
+            a1 = fmaf(w, uyz.x, a1);
+            a2 = fmaf(w, uyz.y, a2);
+          }
+        }
+        u0 += a0;
+        u1 += a1;
+        u2 += a2;
+        return;
+      }
       float sx0 = 0.f, sy0 = 0.f, sz0 = 0.f, sx2 = 0.f, sy2 = 0.f, sz2 = 0.f;
       float dx0 = 0.f, dy0 = 0.f, dz0 = 0.f, dy1 = 0.f, dz1 = 0.f;
 #pragma unroll
