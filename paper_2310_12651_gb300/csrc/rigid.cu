@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(256) rigid_residual_kernel(const R* __restrict
 // M_bb's blocks the FCM pair mobility S(x; sigma sqrt 2) = A(r) I + B(r) x^ x^ of the minimum-image
 // separation (from the Gaussian-regularised Stokeslet terms S1, S2, S3 of Section 2.2) and 1/(6 pi
 // eta a) I on the diagonal. One CTA per body builds A_b in shared memory (entries in FP64, stored in
-// R) and inverts it by Gauss-Jordan elimination with partial pivoting on [A_b | I]; the inverse is
+// R) and inverts it by Gauss-Jordan elimination on [A_b | I] (no row exchanges needed, see below); the inverse is
 // written transposed (column j of A_b^-1 contiguous), stride ms x ms per body, for the residual
 // kernel's coalesced matrix-vector product. flags[1] <- 1 + a body whose pivot vanished.
 
@@ -242,8 +242,6 @@ __global__ void __launch_bounds__(256) body_precond_kernel(const R* __restrict__
   const int k = o1 - o0, m = 3 * k + 6, w2 = 2 * m;
   R* aug = reinterpret_cast<R*>(smraw);            // m x 2m
   R* fac = aug + (size_t)m * w2;                    // m factors of the current column
-  __shared__ int piv_row;
-  __shared__ double piv_val;
   __shared__ int bad;
   if (threadIdx.x == 0) bad = 0;
   // [A_b | I]: identity, the K blocks and zeros element by element, then the mobility blocks pair by
@@ -313,38 +311,20 @@ __global__ void __launch_bounds__(256) body_precond_kernel(const R* __restrict__
     }
   }
   __syncthreads();
+  // Gauss-Jordan without row exchanges: M_bb / mu is symmetric positive definite, so the first 3k
+  // pivots are positive, and the last 6 are those of the Schur complement -K^T (M_bb / mu)^-1 K,
+  // negative definite when K has full column rank (3 particles off one line); a vanishing pivot
+  // flags the body.
   const R tiny = sizeof(R) == 4 ? R(1e-6) : R(1e-12);
   for (int col = 0; col < m; ++col) {
-    if (threadIdx.x < 32) {   // pivot: largest |entry| in rows col..m-1 of this column (lowest row on ties)
-      double best = -1.0;
-      int br = col;
-      for (int r = col + threadIdx.x; r < m; r += 32) {
-        const double v = fabs((double)aug[(size_t)r * w2 + col]);
-        if (v > best) { best = v; br = r; }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int orr = __shfl_xor_sync(0xffffffffu, br, o);
-        if (ob > best || (ob == best && orr < br)) { best = ob; br = orr; }
-      }
-      if (threadIdx.x == 0) {
-        piv_row = br;
-        piv_val = (double)aug[(size_t)br * w2 + col];
-        if (!(fabs(piv_val) > (double)tiny)) bad = 1;
-      }
+    const R pv = aug[(size_t)col * w2 + col];
+    if (!(fabs((double)pv) > (double)tiny)) {
+      if (threadIdx.x == 0) bad = 1;
+      break;   // every thread reads the same pivot, so all leave together
     }
-    __syncthreads();
-    if (bad) break;
-    const int pr = piv_row;
-    const R inv_p = (R)(1.0 / piv_val);
-    for (int c = threadIdx.x; c < w2; c += blockDim.x) {   // swap rows col and pr, scale the pivot row
-      const R vp = aug[(size_t)pr * w2 + c];
-      const R vc = aug[(size_t)col * w2 + c];
-      aug[(size_t)pr * w2 + c] = vc;
-      aug[(size_t)col * w2 + c] = vp * inv_p;
-    }
-    __syncthreads();
+    const R inv_p = R(1) / pv;
+    __syncthreads();   // everyone has read the pivot before row col changes
+    for (int c = threadIdx.x; c < w2; c += blockDim.x) aug[(size_t)col * w2 + c] *= inv_p;
     for (int r = threadIdx.x; r < m; r += blockDim.x) fac[r] = (r == col) ? R(0) : aug[(size_t)r * w2 + col];
     __syncthreads();
     {   // warps over rows, lanes over columns (no division per element)
@@ -359,6 +339,7 @@ __global__ void __launch_bounds__(256) body_precond_kernel(const R* __restrict__
     }
     __syncthreads();
   }
+  __syncthreads();
   R* out = aT + (size_t)b * ms * ms;
   if (bad) {
     if (threadIdx.x == 0) atomicCAS(&flags[1], 0, b + 1);
