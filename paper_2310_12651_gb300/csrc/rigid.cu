@@ -405,8 +405,16 @@ __global__ void __launch_bounds__(256) rigid_residual_body_kernel(const R* __res
     __syncwarp();
     const R* A = aT + (size_t)b * ms * ms;
     for (int i = lane; i < m; i += 32) {
-      R sum = R(0);
-      for (int j = 0; j < m; ++j) sum += A[(size_t)j * ms + i] * v[j];
+      R s0 = R(0), s1 = R(0), s2 = R(0), s3 = R(0);   // four independent chains: loads in flight
+      int j = 0;
+      for (; j + 3 < m; j += 4) {
+        s0 += A[(size_t)j * ms + i] * v[j];
+        s1 += A[(size_t)(j + 1) * ms + i] * v[j + 1];
+        s2 += A[(size_t)(j + 2) * ms + i] * v[j + 2];
+        s3 += A[(size_t)(j + 3) * ms + i] * v[j + 3];
+      }
+      for (; j < m; ++j) s0 += A[(size_t)j * ms + i] * v[j];
+      const R sum = (s0 + s1) + (s2 + s3);
       if (i < 3 * k) z[3 * (size_t)o0 + i] = -sum;
       else z[3 * (size_t)n + 6 * (size_t)b + (i - 3 * k)] = -sum;
     }
