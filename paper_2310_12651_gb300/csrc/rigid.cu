@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(256) rigid_residual_kernel(const R* __restrict
 // M_bb's blocks the FCM pair mobility S(x; sigma sqrt 2) = A(r) I + B(r) x^ x^ of the minimum-image
 // separation (from the Gaussian-regularised Stokeslet terms S1, S2, S3 of Section 2.2) and 1/(6 pi
 // eta a) I on the diagonal. One CTA per body builds A_b in shared memory (entries in FP64, stored in
-// R) and inverts it by Gauss-Jordan elimination on [A_b | I] (no row exchanges needed, see below); the inverse is
+// R) and inverts it in place by Gauss-Jordan elimination (no row exchanges needed, see below); the inverse is
 // written transposed (column j of A_b^-1 contiguous), stride ms x ms per body, for the residual
 // kernel's coalesced matrix-vector product. flags[1] <- 1 + a body whose pivot vanished.
 
@@ -239,19 +239,17 @@ __global__ void __launch_bounds__(256) body_precond_kernel(const R* __restrict__
   const int b = blockIdx.x;
   if (b >= nb) return;
   const int o0 = body_off[b], o1 = body_off[b + 1];
-  const int k = o1 - o0, m = 3 * k + 6, w2 = 2 * m;
-  R* aug = reinterpret_cast<R*>(smraw);            // m x 2m
+  const int k = o1 - o0, m = 3 * k + 6, w2 = m;
+  R* aug = reinterpret_cast<R*>(smraw);            // m x m, inverted in place
   R* fac = aug + (size_t)m * w2;                    // m factors of the current column
   __shared__ int bad;
   if (threadIdx.x == 0) bad = 0;
-  // [A_b | I]: identity, the K blocks and zeros element by element, then the mobility blocks pair by
+  // A_b: the K blocks and zeros element by element, then the mobility blocks pair by
   // pair (one closed form per pair, in the handle's precision)
   for (int e = threadIdx.x; e < m * w2; e += blockDim.x) {
     const int r = e / w2, c = e - r * w2;
     R v = R(0);
-    if (c >= m) {
-      v = (c - m == r) ? R(1) : R(0);
-    } else if (r < 3 * k && c >= 3 * k) {   // -K_i: [-I, [r_i]x], [r]x = [[0, -rz, ry], [rz, 0, -rx], [-ry, rx, 0]]
+    if (r < 3 * k && c >= 3 * k) {   // -K_i: [-I, [r_i]x], [r]x = [[0, -rz, ry], [rz, 0, -rx], [-ry, rx, 0]]
       const int i = r / 3, p = r - 3 * i, q = c - 3 * k;
       const size_t ai = 3 * (size_t)(o0 + i);
       const R rx = arm[ai], ry = arm[ai + 1], rz = arm[ai + 2];
@@ -316,7 +314,7 @@ __global__ void __launch_bounds__(256) body_precond_kernel(const R* __restrict__
   // negative definite when K has full column rank (3 particles off one line); a vanishing pivot
   // flags the body.
   const R tiny = sizeof(R) == 4 ? R(1e-6) : R(1e-12);
-  for (int col = 0; col < m; ++col) {
+  for (int col = 0; col < m; ++col) {   // in-place Gauss-Jordan: after step col, column col holds A^-1's
     const R pv = aug[(size_t)col * w2 + col];
     if (!(fabs((double)pv) > (double)tiny)) {
       if (threadIdx.x == 0) bad = 1;
@@ -324,17 +322,18 @@ __global__ void __launch_bounds__(256) body_precond_kernel(const R* __restrict__
     }
     const R inv_p = R(1) / pv;
     __syncthreads();   // everyone has read the pivot before row col changes
-    for (int c = threadIdx.x; c < w2; c += blockDim.x) aug[(size_t)col * w2 + c] *= inv_p;
+    for (int c = threadIdx.x; c < w2; c += blockDim.x)
+      aug[(size_t)col * w2 + c] = (c == col ? R(1) : aug[(size_t)col * w2 + c]) * inv_p;
     for (int r = threadIdx.x; r < m; r += blockDim.x) fac[r] = (r == col) ? R(0) : aug[(size_t)r * w2 + col];
     __syncthreads();
-    {   // warps over rows, lanes over columns (no division per element)
+    {   // warps over rows, lanes over columns: a[r][c] = (c == col ? 0 : a[r][c]) - f_r a[col][c]
       const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
       for (int r = wid; r < m; r += nw) {
         const R f = fac[r];
-        if (f == R(0)) continue;
+        if (r == col || f == R(0)) continue;
         R* rowr = aug + (size_t)r * w2;
         const R* rowc = aug + (size_t)col * w2;
-        for (int c = col + lane; c < w2; c += 32) rowr[c] -= f * rowc[c];
+        for (int c = lane; c < w2; c += 32) rowr[c] = (c == col ? R(0) : rowr[c]) - f * rowc[c];
       }
     }
     __syncthreads();
@@ -348,7 +347,7 @@ __global__ void __launch_bounds__(256) body_precond_kernel(const R* __restrict__
   }
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) {   // out[j][i] = (A^-1)[i][j]
     const int j = e / m, i = e - j * m;
-    out[(size_t)j * ms + i] = aug[(size_t)i * w2 + m + j];
+    out[(size_t)j * ms + i] = aug[(size_t)i * w2 + j];
   }
 }
 
@@ -539,7 +538,7 @@ template <typename R>
 void launch_body_precond(const R* arm, const int* body_off, int nb, int kmax, const double L[3], double a, double eta,
                          R* aT, int* flags, cudaStream_t s, long long* launches) {
   const int m = 3 * kmax + 6;
-  const size_t smem = sizeof(R) * ((size_t)m * 2 * m + m);
+  const size_t smem = sizeof(R) * ((size_t)m * m + m);
   cudaFuncSetAttribute(body_precond_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   body_precond_kernel<R><<<nb, 256, smem, s>>>(arm, body_off, nb, L[0], L[1], L[2], a, eta, m, aT, flags);
   *launches += 1;
