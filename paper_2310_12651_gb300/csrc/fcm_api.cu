@@ -923,7 +923,8 @@ int rigid_solve(fcm_handle* h, int n, const R* pos, int nb, const int* body_off,
   const double onev = 1.0;
   FCM_CUDA(cudaMemsetAsync(scal, 0, b_scal, s));
   FCM_CUDA(cudaMemcpyAsync(one, &onev, sizeof(double), cudaMemcpyHostToDevice, s));
-  launch_rigid_setup<R>(pos, body_off, X, n, nb, h->p.L, arm, ginv, flags, s, &h->launches);
+  launch_rigid_setup<R>(pos, body_off, X, n, nb, h->p.L, arm, precond == FCM_RIGID_PRECOND_BODY ? nullptr : ginv,
+                        flags, s, &h->launches);
   launch_dot<R>(ft, ft, 6 * (size_t)nb, ftn2, s, &h->launches);
   int hf[4] = {0, 0, 0, 0};
   double hft2 = 0.0;

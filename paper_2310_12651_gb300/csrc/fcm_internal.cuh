@@ -303,7 +303,7 @@ void launch_combine(R* out, const R* V, const LanczosCoef& c, int k, size_t m, b
 // Rigid-body solve (rigid.cu). Unknown and step vectors have length m = 3n + 6 nb, laid out
 // (F of n particles, W/mu of nb bodies); step j of the Broyden history sits at S + j * stride.
 constexpr int kBroydenMax = 256;
-template <typename R>   // lever arms (3n) and (K^T K)^-1 (36 nb); flags[0]: bad offsets, flags[1]: singular
+template <typename R>   // lever arms (3n) and, unless ginv is NULL, (K^T K)^-1 (36 nb); flags[0]: bad offsets, [1]: singular
 void launch_rigid_setup(const R* pos, const int* body_off, const R* X, int n, int nb, const double L[3], R* arm,
                         R* ginv, int* flags, cudaStream_t s, long long* launches);
 template <typename R>   // z = -J0^-1 R(x) for V = M F, *norm2 += ||R||^2

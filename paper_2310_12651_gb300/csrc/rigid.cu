@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(256) rigid_setup_kernel(const R* __restrict__ 
     s[3] += rx * rx; s[4] += ry * ry; s[5] += rz * rz;
     s[6] += rx * ry; s[7] += rx * rz; s[8] += ry * rz;
   }
+  if (ginv == nullptr) return;   // the body preconditioner does not use (K^T K)^-1
 #pragma unroll
   for (int k = 0; k < 9; ++k) s[k] = warp_sum(s[k]);
   const double cnt = (double)(o1 - o0), tr = s[3] + s[4] + s[5];
