@@ -325,16 +325,25 @@ __global__ void __launch_bounds__(256) body_precond_kernel(const R* __restrict__
     __syncthreads();   // everyone has read the pivot before row col changes
     for (int c = threadIdx.x; c < w2; c += blockDim.x)
       aug[(size_t)col * w2 + c] = (c == col ? R(1) : aug[(size_t)col * w2 + c]) * inv_p;
-    for (int r = threadIdx.x; r < m; r += blockDim.x) fac[r] = (r == col) ? R(0) : aug[(size_t)r * w2 + col];
+    for (int r = threadIdx.x; r < m; r += blockDim.x) {   // the factors; column col of the other rows set to 0,
+      if (r == col) { fac[r] = R(0); continue; }           // so that the update below is the same everywhere
+      fac[r] = aug[(size_t)r * w2 + col];
+      aug[(size_t)r * w2 + col] = R(0);
+    }
     __syncthreads();
-    {   // warps over rows, lanes over columns: a[r][c] = (c == col ? 0 : a[r][c]) - f_r a[col][c]
+    {   // warps over rows, lanes over columns (at most 4 per lane: m <= 3 kRigidBodyMax + 6 = 102 < 128)
       const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+      const R* rowc = aug + (size_t)col * w2;
+      R cv[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) cv[t] = (lane + 32 * t < w2) ? rowc[lane + 32 * t] : R(0);
       for (int r = wid; r < m; r += nw) {
         const R f = fac[r];
-        if (r == col || f == R(0)) continue;
+        if (f == R(0)) continue;
         R* rowr = aug + (size_t)r * w2;
-        const R* rowc = aug + (size_t)col * w2;
-        for (int c = lane; c < w2; c += 32) rowr[c] = (c == col ? R(0) : rowr[c]) - f * rowc[c];
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (lane + 32 * t < w2) rowr[lane + 32 * t] -= f * cv[t];
       }
     }
     __syncthreads();
