@@ -49,12 +49,14 @@ def wrap(Y, L):
     return np.where(Yw >= L, Yw - L, Yw)
 
 
-def _windows(Yc, L, M, M_G):
-    """Per dimension: wrapped indices (P, M_G) and displacements x_g - Y (P, M_G)."""
+def _windows(Yc, L, M, M_G, fp32_windows=False):
+    """Per dimension: wrapped indices (P, M_G) and displacements x_g - Y (P, M_G). With fp32_windows
+    the window start is decided in FP32 (params.window_start), as an FP32 path decides it."""
     h = L / M
     idx, dsp = [], []
     for d in range(3):
-        i0 = window_start(Yc[:, d], h[d], M_G)
+        inv = np.float32(M[d] / L[d]) if fp32_windows else None
+        i0 = window_start(Yc[:, d], h[d], M_G, inv)
         ii = i0[:, None] + np.arange(M_G)[None, :]
         dsp.append(ii * h[d] - Yc[:, d][:, None])
         idx.append(np.mod(ii, M[d]))
@@ -78,8 +80,9 @@ def _flat(idx, M):
     return ((ix[:, :, None, None] * M[1] + iy[:, None, :, None]) * M[2] + iz[:, None, None, :])
 
 
-def spread(Y, F, T, L, M, M_G, Sigma, Sigma_D, a=1.0, chunk=512):
-    """Force density on the grid, shape (3, M_x, M_y, M_z)."""
+def spread(Y, F, T, L, M, M_G, Sigma, Sigma_D, a=1.0, chunk=512, fp32_windows=False):
+    """Force density on the grid, shape (3, M_x, M_y, M_z). fp32_windows: window starts decided in
+    FP32 (for checking an FP32 path on particles that sit on grid points)."""
     L, M = _as3(L), _as3(M, np.int64)
     Yw = wrap(Y, L)
     n = Yw.shape[0]
@@ -88,7 +91,7 @@ def spread(Y, F, T, L, M, M_G, Sigma, Sigma_D, a=1.0, chunk=512):
     f = np.zeros((3, size))
     for s in range(0, n, chunk):
         Yc = Yw[s:s + chunk]
-        idx, dsp = _windows(Yc, L, M, M_G)
+        idx, dsp = _windows(Yc, L, M, M_G, fp32_windows)
         g_mod, gD = _kernel_values(dsp, Sigma, Sigma_D, sigma)
         flat = _flat(idx, M).ravel()
         Fc = np.asarray(F[s:s + chunk], dtype=np.float64)

@@ -21,9 +21,18 @@ import numpy as np
 from . import closed_forms as cf
 
 
-def window_start(Y, h, M_G):
-    """First grid index of the M_G-point window around coordinate Y (unwrapped, may be < 0)."""
-    return np.floor(np.asarray(Y, dtype=np.float64) / h - 0.5 * M_G).astype(np.int64) + 1
+def window_start(Y, h, M_G, inv_h32=None):
+    """First grid index of the M_G-point window around coordinate Y (unwrapped, may be < 0):
+    floor(Y/h - M_G/2) + 1 (Section 4 places the window; it does not fix a precision).
+
+    The window start is an integer decided by floating point, so a check of an FP32 path takes the
+    decision in FP32 like that path: with inv_h32 = fl32(M/L) given, s = fl32(fl32(Y) * inv_h32) and
+    the floor of fl32(s - M_G/2). Away from the points where Y/h - M_G/2 is an integer (a particle on
+    a grid point, for even M_G) both readings give the same index."""
+    if inv_h32 is None:
+        return np.floor(np.asarray(Y, dtype=np.float64) / h - 0.5 * M_G).astype(np.int64) + 1
+    s = np.asarray(Y, dtype=np.float32) * np.float32(inv_h32)
+    return np.floor(s - np.float32(0.5 * M_G)).astype(np.int64) + 1
 
 
 def support_points(Sigma, h, c=4.0):

@@ -249,6 +249,33 @@ def test_window_is_the_nearest_points(MG):
     assert np.all(np.minimum(np.abs(before), np.abs(after)) >= np.max(np.abs(d), axis=1) - 1e-12)
 
 
+@pytest.mark.parametrize("MG", [10, 12, 14])
+def test_fp32_window_decision(MG):
+    """Window starts decided in FP32 (params.window_start with inv_h32, as an FP32 path decides them)
+    equal the FP64 decision away from ties; for a particle on a grid point k (a tie for even M_G)
+    either decision is one of the two nearest-point windows, so it holds k at position M_G/2 - 1 or
+    M_G/2; and without ties the FP32-decided spread is the FP64-decided one."""
+    L, M = 48.0, 40
+    h = L / M
+    inv = np.float32(M / L)
+    rng = np.random.default_rng(17)
+    Y = rng.random(20000).astype(np.float32).astype(np.float64) * np.float32(L)
+    a, b = pr.window_start(Y, h, MG), pr.window_start(Y, h, MG, inv)
+    s = Y / h - 0.5 * MG
+    away = np.abs(s - np.round(s)) > 1e-5
+    assert np.array_equal(a[away], b[away])
+    k = np.arange(4 * M)
+    Yk = (k * h).astype(np.float32).astype(np.float64)
+    b = pr.window_start(Yk, h, MG, inv)
+    assert set(np.unique(b - (k - MG // 2))) <= {0, 1}
+    Y3 = np.array([[5.1, 7.7, 30.3], [17.3, 44.9, 2.2], [47.9, 0.05, 23.3]])
+    F = np.array([[0.3, -1.1, 0.7], [1.0, 0.2, -0.4], [-0.6, 0.5, 0.9]])
+    T = np.array([[0.2, 0.1, -0.3], [-0.5, 0.4, 0.6], [0.7, -0.2, 0.1]])
+    f32 = g.spread(Y3, F, T, L, M, MG, 2.0, 1.7, fp32_windows=True)
+    f64 = g.spread(Y3, F, T, L, M, MG, 2.0, 1.7)
+    assert np.array_equal(f32, f64)
+
+
 def test_cutoff_rule_against_table2():
     """Our pointwise R_c rule lands on the paper's empirical slopes lambda (Table 2) within 8%."""
     rows = {float(r[0]): [float(v) for v in r[1:]] for r in _golden("table2_cutoff_slope.txt")}
