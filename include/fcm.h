@@ -75,7 +75,10 @@ typedef struct fcm_params {
   int max_n;         /* capacity: largest n accepted by fcm_apply                         */
   int tile[3];       /* FP32 spread/gather tile in grid points per dimension; 0 = choose */
   int spread_kernel; /* FP32 spread: 0 = choose, 1 = row-stationary (registers, no      */
-                     /* atomics; needs tile[0] == 8 and M_G <= 16), 2 = shared atomics   */
+                     /* atomics; needs tile[0] == 8 and M_G <= 16), 2 = shared atomics,  */
+                     /* 3 = tensor cores (tcgen05, TF32 operands split in three products */
+                     /* for FP32 accuracy; 8^3 tiles and M_G in {10, 12, 14}, otherwise  */
+                     /* as 0)                                                            */
 } fcm_params;
 
 typedef struct fcm_handle fcm_handle;
@@ -253,7 +256,8 @@ int fcm_spread(fcm_handle* h, int n, const void* pos, const void* F, const void*
 
 /* Waits (bounded by timeout_ms, polling) for all work the handle enqueued on
  * `stream`, then reads and clears the device status word into *flags
- * (bit 0: a non-finite position was seen). Returns FCM_ERR_TIMEOUT if the
+ * (bit 0: a non-finite position was seen; bit 1: a bounded wait inside a
+ * kernel ran out, so that pass's result is incomplete). Returns FCM_ERR_TIMEOUT if the
  * wait ran out, FCM_ERR_INPUT if flags != 0. */
 int fcm_check(fcm_handle* h, void* stream, int timeout_ms, int* flags);
 

@@ -15,7 +15,8 @@ constexpr int kSeriesTerms = 10;   // Taylor terms of the small-r branch
 constexpr int kMaxMG = 24;         // largest grid support the kernels accept
 
 // Status bits written by kernels into the handle's device status word.
-enum : int { kStatusNonFinite = 1 };
+// kStatusWaitTimeout: a bounded wait inside a kernel ran out (that kernel's output is incomplete).
+enum : int { kStatusNonFinite = 1, kStatusWaitTimeout = 2 };
 
 // ---------------------------------------------------------------- vectors
 template <typename R> struct Vec4;
@@ -81,8 +82,10 @@ __device__ inline R wrap_coord(R y, R L, int* bad) {
 }
 
 // First grid index of the M_G-point window: floor(y/h - M_G/2) + 1 (unwrapped),
-// from s = y/h. The FP32 path forms s = y * (1/h) and the FP64 path s = y / h;
-// every site of one precision goes through window_start_d, so they all agree.
+// from s = y/h. The FP32 path forms s = y * (1/h) with the product rounded on its
+// own (no contraction of y * (1/h) - M_G/2 into one FMA, which would move the
+// floor for a particle on a grid point), the FP64 path s = y / h; every site of
+// one precision goes through window_start_d, so they all agree.
 template <typename R>
 __device__ inline int window_start_scaled(R s, int MG) {
   R v = x_floor(s - R(0.5) * R(MG));
@@ -95,7 +98,7 @@ template <typename T>
 __host__ __device__ inline T sel3(const T (&a)[3], int d) { return d == 0 ? a[0] : (d == 1 ? a[1] : a[2]); }
 
 __device__ inline int window_start_d(const Geometry<float>& g, int d, float y) {
-  return window_start_scaled(y * sel3(g.inv_h, d), g.MG);
+  return window_start_scaled(x_mul_rn(y, sel3(g.inv_h, d)), g.MG);
 }
 __device__ inline int window_start_d(const Geometry<double>& g, int d, double y) {
   return window_start_scaled(y / sel3(g.h, d), g.MG);
@@ -334,9 +337,14 @@ size_t tile_smem_bytes(const int tile[3], int MG);      // extended region (gath
 size_t spread_smem_bytes(const int tile[3], int MG);    // whichever spread kernel the tile selects
 bool spread_uses_rows(const int tile[3], int MG);       // row-stationary spread applies
 int tile_smem_limit();
-// spread_kernel: 0 = choose, 1 = row-stationary, 2 = shared atomics (fcm_params.spread_kernel).
+// spread_kernel: 0 = choose, 1 = row-stationary, 2 = shared atomics, 3 = tensor cores where eligible
+// (fcm_params.spread_kernel).
 void launch_spread_f32(const Geometry<float>& g, const KernelConsts<float>& kc, bool torque, int spread_kernel,
                        const BinBuffers& b, float* grid, cudaStream_t s, long long* launches);
+// Tensor-core spread (spread_mma.cu): 8^3 tiles and M_G in {10, 12, 14}.
+bool spread_mma_eligible(const int tile[3], int MG);
+void launch_spread_mma(const Geometry<float>& g, const KernelConsts<float>& kc, bool torque, const BinBuffers& b,
+                       float* grid, cudaStream_t s);
 void launch_gather_f32(const Geometry<float>& g, const KernelConsts<float>& kc, bool torque,
                        const BinBuffers& b, const float* grid, const float* upair, const float* wpair,
                        float* U, float* W, cudaStream_t s, long long* launches);

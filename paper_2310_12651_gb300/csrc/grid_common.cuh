@@ -157,6 +157,36 @@ __device__ inline void flush_region(const Geometry<float>& g, const TileOrigin& 
   }
 }
 
+// TX = 8: one binning tile per CTA. TX = 16: two x-adjacent binning tiles (8 points each) per CTA;
+// their particles are contiguous in the tile-sorted order (tiles are numbered x fastest), and the
+// wider rows add about a third less halo to the grid per grid point.
+template <int TX>
+__device__ inline bool spread_tile_range(const Geometry<float>& g, const int* __restrict__ tstart, int b, int* p0,
+                                         int* p1, TileOrigin* o, size_t* goff) {
+  if (TX == 8) {
+    *p0 = tstart[b];
+    *p1 = tstart[b + 1];
+    if (*p0 >= *p1) return false;
+    *o = tile_origin(g, local_tile(g, b, goff));
+    return true;
+  }
+  const int ntx = g.ntile[0], nsx = (ntx + 1) >> 1;
+  const int sper = nsx * g.ntile[1] * g.ntile[2];
+  const int sys = b / sper;
+  const int sl = b - sys * sper;
+  const int sx = sl % nsx, rest = sl / nsx;
+  const int t0 = sys * g.tiles_per + 2 * sx + ntx * rest;
+  const int t1 = t0 + ((2 * sx + 1 < ntx) ? 2 : 1);
+  *p0 = tstart[t0];
+  *p1 = tstart[t1];
+  if (*p0 >= *p1) return false;
+  *goff = (size_t)sys * (size_t)g.grid_stride;
+  o->ox0 = 2 * sx * g.tile[0];
+  o->oy0 = (rest % g.ntile[1]) * g.tile[1];
+  o->oz0 = (rest / g.ntile[1]) * g.tile[2];
+  return true;
+}
+
 // Global reduction of four consecutive floats (16-byte aligned address).
 __device__ inline void red_add_v4(float* p, float a, float b, float c, float d) {
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)

@@ -90,36 +90,6 @@ constexpr int rows_threads(int MGT) {
   return MGT <= 14 ? (((7 + MGT) * (7 + MGT) + 31) / 32) * 32 : kRowsMaxThreads;
 }
 
-// TX = 8: one binning tile per CTA. TX = 16: two x-adjacent binning tiles (8 points each) per CTA;
-// their particles are contiguous in the tile-sorted order (tiles are numbered x fastest), and the
-// wider rows add about a third less halo to the grid per grid point.
-template <int TX>
-__device__ inline bool spread_tile_range(const Geometry<float>& g, const int* __restrict__ tstart, int b, int* p0,
-                                         int* p1, TileOrigin* o, size_t* goff) {
-  if (TX == 8) {
-    *p0 = tstart[b];
-    *p1 = tstart[b + 1];
-    if (*p0 >= *p1) return false;
-    *o = tile_origin(g, local_tile(g, b, goff));
-    return true;
-  }
-  const int ntx = g.ntile[0], nsx = (ntx + 1) >> 1;
-  const int sper = nsx * g.ntile[1] * g.ntile[2];
-  const int sys = b / sper;
-  const int sl = b - sys * sper;
-  const int sx = sl % nsx, rest = sl / nsx;
-  const int t0 = sys * g.tiles_per + 2 * sx + ntx * rest;
-  const int t1 = t0 + ((2 * sx + 1 < ntx) ? 2 : 1);
-  *p0 = tstart[t0];
-  *p1 = tstart[t1];
-  if (*p0 >= *p1) return false;
-  *goff = (size_t)sys * (size_t)g.grid_stride;
-  o->ox0 = 2 * sx * g.tile[0];
-  o->oy0 = (rest % g.ntile[1]) * g.tile[1];
-  o->oz0 = (rest / g.ntile[1]) * g.tile[2];
-  return true;
-}
-
 template <int MGT, bool GUARD, bool TORQUE, bool SAMEW, int TX>
 __global__ void __launch_bounds__(rows_threads(MGT), 1) spread_rows_kernel(Geometry<float> g, KernelConsts<float> kc,
                                                                         const float4* __restrict__ pos,
@@ -410,7 +380,9 @@ static void atomic_variant(const Geometry<float>& g, const KernelConsts<float>& 
 
 void launch_spread_f32(const Geometry<float>& g, const KernelConsts<float>& kc, bool torque, int spread_kernel,
                        const BinBuffers& b, float* grid, cudaStream_t s, long long* launches) {
-  if (rows_selected(g, spread_kernel)) {
+  if (spread_kernel == 3 && spread_mma_eligible(g.tile, g.MG)) {
+    launch_spread_mma(g, kc, torque, b, grid, s);
+  } else if (rows_selected(g, spread_kernel)) {
 #define ROWS_CALL(MGT, GUARD)                                                              \
   if (!torque) rows_variant<MGT, GUARD, false, true>(g, kc, b, grid, s);                  \
   else if (kc.same_width) rows_variant<MGT, GUARD, true, true>(g, kc, b, grid, s);        \
