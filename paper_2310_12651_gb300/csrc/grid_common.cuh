@@ -193,9 +193,14 @@ __device__ inline void red_add_v4(float* p, float a, float b, float c, float d) 
                : "memory");
 }
 
+// Pairs of x points per particle in the row-stationary spread: the window's M_G points placed on
+// even-aligned pairs of the row (one zero in front when the window starts on an odd point, one
+// behind when it starts on an even one), M_G / 2 + 1 pairs.
+__host__ __device__ constexpr int row_pairs(int MGT) { return MGT / 2 + 1; }
+
 // Per-particle profile tables staged in shared memory (row-stationary spread).
 struct RowTables {
-  float4* xt;   // [chunk][MGT] {g, d^2 g, d g_D, g_D} along x
+  float4* xp;   // [chunk][pairs][2] {g, g', d^2 g, (d^2 g)'}, {d g_D, (d g_D)', g_D, g_D'} along x, ' = next point
   float4* yt;   // [chunk][MGT] {g, d, g_D, 0} along y
   float4* zt;   // [chunk][MGT] {g, d, g_D, 0} along z
   float4* pf;   // [chunk] force
@@ -206,8 +211,8 @@ struct RowTables {
 template <int MGT>
 __device__ inline RowTables row_tables(float4* sm) {
   RowTables t;
-  t.xt = sm;
-  t.yt = t.xt + kRowsChunk * MGT;
+  t.xp = sm;
+  t.yt = t.xp + kRowsChunk * 2 * row_pairs(MGT);
   t.zt = t.yt + kRowsChunk * MGT;
   t.pf = t.zt + kRowsChunk * MGT;
   t.pt = t.pf + kRowsChunk;
@@ -216,7 +221,8 @@ __device__ inline RowTables row_tables(float4* sm) {
 }
 
 __host__ __device__ constexpr size_t row_tables_bytes(int MGT) {
-  return sizeof(float4) * (3 * (size_t)kRowsChunk * MGT + 2 * kRowsChunk) + sizeof(int4) * kRowsChunk;
+  return sizeof(float4) * ((size_t)kRowsChunk * (2 * row_pairs(MGT) + 2 * MGT) + 2 * kRowsChunk) +
+         sizeof(int4) * kRowsChunk;
 }
 
 // Kernel variants: MGT is the compiled support; GUARD says whether the runtime

@@ -20,67 +20,78 @@
 
 namespace fcm {
 
-// Forces only: the row's weight at each point, w = GQ g + GB d^2 g, is formed once and scaled by the
-// three force components (5 operations per point); with torques the terms are kept per component.
-template <int OX, int MGT, int EXT, bool GUARD, bool TORQUE, bool SAMEW>
-__device__ __forceinline__ void add_row(const float4* __restrict__ xt, int MG, float (&sx)[EXT], float (&sy)[EXT],
-                                        float (&sz)[EXT], float ax, float ay, float az, float bx, float by, float bz,
-                                        float cx, float cy, float cz, float ky, float kz, float gq, float gb,
-                                        float4 f) {
+// The row update works on pairs of x points with packed FP32 instructions (__ffma2_rn: two
+// correctly rounded FMAs per instruction, the same operations in the same order as one FMA per
+// point). Forces only: the row's weight at each point, w = GQ g + GB d^2 g, is formed once and scaled
+// by the three force components; with torques the terms are kept per component.
+template <int OXP, int NP, int EXT2, bool TORQUE, bool SAMEW>
+__device__ __forceinline__ void add_row2(const float4* __restrict__ xp, float2 (&sx)[EXT2], float2 (&sy)[EXT2],
+                                         float2 (&sz)[EXT2], float ax, float ay, float az, float bx, float by,
+                                         float bz, float cx, float cy, float cz, float ky, float kz, float gq,
+                                         float gb, float4 f) {
+  static_assert(OXP + NP <= EXT2, "pair window beyond the row");
+  const float2 AX = make_float2(ax, ax), AY = make_float2(ay, ay), AZ = make_float2(az, az);
+  const float2 BX = make_float2(bx, bx), BY = make_float2(by, by), BZ = make_float2(bz, bz);
 #pragma unroll
-  for (int j = 0; j < MGT; ++j) {
-    if (!GUARD || j < MG) {
-      const float4 xv = xt[j];
-      if (!TORQUE) {
-        const float w = fmaf(gb, xv.y, gq * xv.x);
-        sx[OX + j] = fmaf(f.x, w, sx[OX + j]);
-        sy[OX + j] = fmaf(f.y, w, sy[OX + j]);
-        sz[OX + j] = fmaf(f.z, w, sz[OX + j]);
-        continue;
-      }
-      float vx = fmaf(bx, xv.y, fmaf(ax, xv.x, sx[OX + j]));
-      float vy = fmaf(by, xv.y, fmaf(ay, xv.x, sy[OX + j]));
-      float vz = fmaf(bz, xv.y, fmaf(az, xv.x, sz[OX + j]));
-      if (TORQUE) {
-        vy = fmaf(ky, xv.z, vy);
-        vz = fmaf(kz, xv.z, vz);
-        if (!SAMEW) {
-          vx = fmaf(cx, xv.w, vx);
-          vy = fmaf(cy, xv.w, vy);
-          vz = fmaf(cz, xv.w, vz);
-        }
-      }
-      sx[OX + j] = vx;
-      sy[OX + j] = vy;
-      sz[OX + j] = vz;
+  for (int jp = 0; jp < NP; ++jp) {
+    const float4 p0 = xp[2 * jp];
+    const float2 g2 = make_float2(p0.x, p0.y), q2 = make_float2(p0.z, p0.w);
+    if (!TORQUE) {
+      const float2 w = __ffma2_rn(make_float2(gb, gb), q2, __fmul2_rn(make_float2(gq, gq), g2));
+      sx[OXP + jp] = __ffma2_rn(make_float2(f.x, f.x), w, sx[OXP + jp]);
+      sy[OXP + jp] = __ffma2_rn(make_float2(f.y, f.y), w, sy[OXP + jp]);
+      sz[OXP + jp] = __ffma2_rn(make_float2(f.z, f.z), w, sz[OXP + jp]);
+      continue;
     }
+    const float4 p1 = xp[2 * jp + 1];
+    const float2 k2 = make_float2(p1.x, p1.y);
+    float2 vx = __ffma2_rn(BX, q2, __ffma2_rn(AX, g2, sx[OXP + jp]));
+    float2 vy = __ffma2_rn(BY, q2, __ffma2_rn(AY, g2, sy[OXP + jp]));
+    float2 vz = __ffma2_rn(BZ, q2, __ffma2_rn(AZ, g2, sz[OXP + jp]));
+    vy = __ffma2_rn(make_float2(ky, ky), k2, vy);
+    vz = __ffma2_rn(make_float2(kz, kz), k2, vz);
+    if (!SAMEW) {
+      const float2 d2 = make_float2(p1.z, p1.w);
+      vx = __ffma2_rn(make_float2(cx, cx), d2, vx);
+      vy = __ffma2_rn(make_float2(cy, cy), d2, vy);
+      vz = __ffma2_rn(make_float2(cz, cz), d2, vz);
+    }
+    sx[OXP + jp] = vx;
+    sy[OXP + jp] = vy;
+    sz[OXP + jp] = vz;
   }
 }
 
-template <int EXT, bool GUARD>
-__device__ __forceinline__ void flush_row(const Geometry<float>& g, const TileOrigin& o, int EX, float* __restrict__ row,
-                                          const float (&s)[EXT]) {
+// Adds a row of EX points (held as pairs) to the grid row starting at x = o.ox0.
+template <int EXT2>
+__device__ inline void flush_row2(const Geometry<float>& g, const TileOrigin& o, int EX, float* __restrict__ row,
+                                  const float2 (&s)[EXT2]) {
   const bool vec = (o.ox0 + EX <= g.M[0]) && ((g.M[0] & 3) == 0);
   if (vec) {
     float* p = row + o.ox0;
 #pragma unroll
-    for (int k = 0; k + 3 < EXT; k += 4) {
-      if (!GUARD || k + 3 < EX) {
-        if (s[k] != 0.f || s[k + 1] != 0.f || s[k + 2] != 0.f || s[k + 3] != 0.f)
-          red_add_v4(p + k, s[k], s[k + 1], s[k + 2], s[k + 3]);
+    for (int k = 0; k + 1 < EXT2; k += 2) {   // points 2k .. 2k + 3
+      if (2 * k + 3 < EX) {
+        if (s[k].x != 0.f || s[k].y != 0.f || s[k + 1].x != 0.f || s[k + 1].y != 0.f)
+          red_add_v4(p + 2 * k, s[k].x, s[k].y, s[k + 1].x, s[k + 1].y);
       } else {
+        const float v[4] = {s[k].x, s[k].y, s[k + 1].x, s[k + 1].y};
 #pragma unroll
         for (int e = 0; e < 4; ++e)
-          if (k + e < EX && s[k + e] != 0.f) atomicAdd(p + k + e, s[k + e]);
+          if (2 * k + e < EX && v[e] != 0.f) atomicAdd(p + 2 * k + e, v[e]);
       }
     }
-#pragma unroll
-    for (int k = (EXT / 4) * 4; k < EXT; ++k)
-      if ((!GUARD || k < EX) && s[k] != 0.f) atomicAdd(p + k, s[k]);
+    if (EXT2 & 1) {
+      const int k = EXT2 - 1;
+      if (2 * k < EX && s[k].x != 0.f) atomicAdd(p + 2 * k, s[k].x);
+      if (2 * k + 1 < EX && s[k].y != 0.f) atomicAdd(p + 2 * k + 1, s[k].y);
+    }
   } else {
 #pragma unroll
-    for (int k = 0; k < EXT; ++k)
-      if ((!GUARD || k < EX) && s[k] != 0.f) atomicAdd(row + wrap_index(o.ox0 + k, g.M[0]), s[k]);
+    for (int k = 0; k < EXT2; ++k) {
+      if (2 * k < EX && s[k].x != 0.f) atomicAdd(row + wrap_index(o.ox0 + 2 * k, g.M[0]), s[k].x);
+      if (2 * k + 1 < EX && s[k].y != 0.f) atomicAdd(row + wrap_index(o.ox0 + 2 * k + 1, g.M[0]), s[k].y);
+    }
   }
 }
 
@@ -98,6 +109,9 @@ __global__ void __launch_bounds__(rows_threads(MGT), 1) spread_rows_kernel(Geome
                                                                         const int* __restrict__ tstart,
                                                                         float* __restrict__ grid) {
   constexpr int EXT = TX + MGT - 1;
+  constexpr int NP = row_pairs(MGT);
+  constexpr int EXT2 = (TX + 2 * NP - 1) / 2;   // pairs of the row: window pairs start at pair (window start) / 2
+  static_assert(2 * EXT2 >= EXT, "row pairs");
   extern __shared__ float4 sm4[];
   int p0, p1;
   size_t goff;
@@ -111,30 +125,57 @@ __global__ void __launch_bounds__(rows_threads(MGT), 1) spread_rows_kernel(Geome
   const bool has_row = row < R;
   const int ez = has_row ? row / EY : 0;
   const int ey = has_row ? row - ez * EY : 0;
-  float sx[EXT], sy[EXT], sz[EXT];
+  float2 sx[EXT2], sy[EXT2], sz[EXT2];
 #pragma unroll
-  for (int k = 0; k < EXT; ++k) { sx[k] = 0.f; sy[k] = 0.f; sz[k] = 0.f; }
+  for (int k = 0; k < EXT2; ++k) {
+    sx[k] = make_float2(0.f, 0.f);
+    sy[k] = make_float2(0.f, 0.f);
+    sz[k] = make_float2(0.f, 0.f);
+  }
   const RowTables tb = row_tables<MGT>(sm4);
 
   for (int base = p0; base < p1; base += kRowsChunk) {
     const int np = min(kRowsChunk, p1 - base);
     __syncthreads();
-    for (int k = threadIdx.x; k < np * 3 * MGT; k += blockDim.x) {
-      const int q = k / (3 * MGT);
-      const int rem = k - q * 3 * MGT;
-      const int d = rem / MGT;
-      const int j = rem - d * MGT;
+    // y and z profiles {g, d, g_D, 0}
+    for (int k = threadIdx.x; k < np * 2 * MGT; k += blockDim.x) {
+      const int q = k / (2 * MGT);
+      const int rem = k - q * 2 * MGT;
+      const int d = 1 + rem / MGT;
+      const int j = rem - (d - 1) * MGT;
       const float4 y = pos[base + q];
-      const float yd = d == 0 ? y.x : (d == 1 ? y.y : y.z);
-      const float h = sel3(g.h, d);
+      const float yd = d == 1 ? y.y : y.z;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
       if (j < MG) {
-        const float dd = (float)(window_start_d(g, d, yd) + j) * h - yd;
+        const float dd = (float)(window_start_d(g, d, yd) + j) * sel3(g.h, d) - yd;
         const float gs = expf(-dd * dd * kc.inv2S2);
         const float gd = SAMEW ? gs : expf(-dd * dd * kc.inv2SD2);
-        v = (d == 0) ? make_float4(gs, dd * dd * gs, dd * gd, gd) : make_float4(gs, dd, gd, 0.f);
+        v = make_float4(gs, dd, gd, 0.f);
       }
-      (d == 0 ? tb.xt : (d == 1 ? tb.yt : tb.zt))[q * MGT + j] = v;
+      (d == 1 ? tb.yt : tb.zt)[q * MGT + j] = v;
+    }
+    // x profiles on even-aligned pairs: slot 2 jp + e holds window point j = 2 jp + e - (start & 1)
+    for (int k = threadIdx.x; k < np * 2 * NP; k += blockDim.x) {
+      const int q = k / (2 * NP);
+      const int slot = k - q * 2 * NP;
+      const float4 y = pos[base + q];
+      const int i0 = window_start_d(g, 0, y.x);
+      const int ox = TX == 8 ? min(max(wrap_once(i0, g.M[0]) - o.ox0, 0), g.tile[0] - 1)
+                             : min(max(wrap_once(i0, g.M[0]) - o.ox0, 0), TX - 1);
+      const int j = slot - (ox & 1);
+      float gs = 0.f, q2 = 0.f, dg = 0.f, gd = 0.f;
+      if (j >= 0 && j < MG) {
+        const float dd = (float)(i0 + j) * g.h[0] - y.x;
+        gs = expf(-dd * dd * kc.inv2S2);
+        gd = SAMEW ? gs : expf(-dd * dd * kc.inv2SD2);
+        q2 = dd * dd * gs;
+        dg = dd * gd;
+      }
+      float* e = reinterpret_cast<float*>(tb.xp + (size_t)(q * NP + (slot >> 1)) * 2) + (slot & 1);
+      e[0] = gs;
+      e[2] = q2;
+      e[4] = dg;
+      e[6] = gd;
     }
     for (int q = threadIdx.x; q < np; q += blockDim.x) {
       int4 off = window_offset(g, o, window_starts(g, pos[base + q]));
@@ -172,20 +213,19 @@ __global__ void __launch_bounds__(rows_threads(MGT), 1) spread_rows_kernel(Geome
         kz = -H * tq.y;
         if (SAMEW) { ax += cx; ay += cy; az += cz; }
       }
-      const float4* xt = tb.xt + q * MGT;
-#define FCM_ROW_CASE(OX)                                                                                     \
-  case OX:                                                                                                   \
-    add_row<OX, MGT, EXT, GUARD, TORQUE, SAMEW>(xt, MG, sx, sy, sz, ax, ay, az, bx, by, bz, cx, cy, cz, ky, kz, GQ, \
-                                                GB, f);                                                          \
+      const float4* xp = tb.xp + (size_t)q * 2 * NP;
+#define FCM_ROW_CASE(OXP)                                                                                 \
+  case OXP:                                                                                               \
+    add_row2<OXP, NP, EXT2, TORQUE, SAMEW>(xp, sx, sy, sz, ax, ay, az, bx, by, bz, cx, cy, cz, ky, kz, GQ, GB, \
+                                           f);                                                            \
     break;
-      switch (off.x) {
+      switch (off.x >> 1) {
         FCM_ROW_CASE(0) FCM_ROW_CASE(1) FCM_ROW_CASE(2) FCM_ROW_CASE(3)
-        FCM_ROW_CASE(4) FCM_ROW_CASE(5) FCM_ROW_CASE(6) FCM_ROW_CASE(7)
         default:
           if (TX > 8) {
-            switch (off.x) {
-              FCM_ROW_CASE(8 % TX) FCM_ROW_CASE(9 % TX) FCM_ROW_CASE(10 % TX) FCM_ROW_CASE(11 % TX)
-              FCM_ROW_CASE(12 % TX) FCM_ROW_CASE(13 % TX) FCM_ROW_CASE(14 % TX) FCM_ROW_CASE(15 % TX)
+            switch (off.x >> 1) {
+              FCM_ROW_CASE(4 % (TX / 2)) FCM_ROW_CASE(5 % (TX / 2)) FCM_ROW_CASE(6 % (TX / 2))
+              FCM_ROW_CASE(7 % (TX / 2))
               default: break;
             }
           }
@@ -200,9 +240,9 @@ __global__ void __launch_bounds__(rows_threads(MGT), 1) spread_rows_kernel(Geome
     const int gz = wrap_index(o.oz0 + ez, g.M[2]);
     float* r0 = grid + ((size_t)gz * g.M[1] + gy) * g.M[0];
     const int EX = TX + MG - 1;
-    flush_row<EXT, GUARD>(g, o, EX, r0, sx);
-    flush_row<EXT, GUARD>(g, o, EX, r0 + Mtot, sy);
-    flush_row<EXT, GUARD>(g, o, EX, r0 + 2 * Mtot, sz);
+    flush_row2<EXT2>(g, o, EX, r0, sx);
+    flush_row2<EXT2>(g, o, EX, r0 + Mtot, sy);
+    flush_row2<EXT2>(g, o, EX, r0 + 2 * Mtot, sz);
   }
 }
 
