@@ -51,7 +51,7 @@ WORKLOADS = {
 }
 # dram__bytes_read.sum + dram__bytes_write.sum per system of a launch (cold caches), from one ncu capture of
 # the current kernels; a launch over B systems moves B times this. None once a kernel changes after the capture.
-TRAFFIC_BYTES = {"c2": {"spread": 28.69e6, "gather": 26.56e6, "pair": 3.18e6}}
+TRAFFIC_BYTES = {"c2": {"spread": 28.90e6, "gather": 26.61e6, "pair": 3.18e6}}
 
 
 def workload(name="c2", n=None, h_ref=None):
