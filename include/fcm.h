@@ -254,11 +254,15 @@ int fcm_copy_grid(fcm_handle* h, void* dst, void* stream);
 /* Sort and spread only: afterwards the grid holds f (Section 4, steps 1-3). */
 int fcm_spread(fcm_handle* h, int n, const void* pos, const void* F, const void* T, void* stream);
 
+/* Bits of the device status word that fcm_check reports. */
+#define FCM_STATUS_NONFINITE 1    /* a non-finite position was seen (clamped, no fault)        */
+#define FCM_STATUS_WAIT_TIMEOUT 2 /* a bounded wait inside a kernel ran out: that pass's result */
+                                  /* is incomplete                                              */
+
 /* Waits (bounded by timeout_ms, polling) for all work the handle enqueued on
  * `stream`, then reads and clears the device status word into *flags
- * (bit 0: a non-finite position was seen; bit 1: a bounded wait inside a
- * kernel ran out, so that pass's result is incomplete). Returns FCM_ERR_TIMEOUT if the
- * wait ran out, FCM_ERR_INPUT if flags != 0. */
+ * (FCM_STATUS_* bits). Returns FCM_ERR_TIMEOUT if the wait ran out,
+ * FCM_ERR_INPUT if flags != 0. */
 int fcm_check(fcm_handle* h, void* stream, int timeout_ms, int* flags);
 
 /* Per-stage timing with CUDA events recorded on the stream each stage runs on.

@@ -731,6 +731,8 @@ void jacobi_eig(std::vector<double> A, int n, std::vector<double>* w, std::vecto
 }
 
 static_assert(kLanczosMax == FCM_LANCZOS_MAX_ITER, "the Lanczos coefficient block holds every iteration");
+static_assert(kStatusNonFinite == FCM_STATUS_NONFINITE && kStatusWaitTimeout == FCM_STATUS_WAIT_TIMEOUT,
+              "device status bits as the header names them");
 
 // Lanczos coefficients c = |z| T^{1/2} e_1 for the k x k tridiagonal T (diagonal alpha, off-diagonal
 // beta): the square root applied to z is then V c. False if T is not positive definite.

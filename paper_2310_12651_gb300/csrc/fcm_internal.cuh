@@ -14,7 +14,7 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr int kSeriesTerms = 10;   // Taylor terms of the small-r branch
 constexpr int kMaxMG = 24;         // largest grid support the kernels accept
 
-// Status bits written by kernels into the handle's device status word.
+// Status bits written by kernels into the handle's device status word (FCM_STATUS_* in fcm.h).
 // kStatusWaitTimeout: a bounded wait inside a kernel ran out (that kernel's output is incomplete).
 enum : int { kStatusNonFinite = 1, kStatusWaitTimeout = 2 };
 

@@ -133,6 +133,9 @@ BROYDEN_MAX_ITER = 256
 RIGID_PRECOND_DIAGONAL, RIGID_PRECOND_BODY = 0, 1
 RIGID_BODY_MAX = 32
 
+#: bits of the device status word returned by Handle.check (include/fcm.h)
+STATUS_NONFINITE, STATUS_WAIT_TIMEOUT = 1, 2
+
 #: capacity of fcm_pair_correction_noalloc's fixed scratch (include/fcm.h)
 NOALLOC_MAX_N = 65536
 NOALLOC_MAX_CELLS = 65536

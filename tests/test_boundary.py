@@ -135,5 +135,7 @@ def test_rigid_solve_rejects_a_null_handle_on_the_host(fcm):
     header = open(os.path.join(ROOT, "include", "fcm.h")).read()
     for name, value in (("FCM_BROYDEN_MAX_ITER", fcm.BROYDEN_MAX_ITER), ("FCM_RIGID_BODY_MAX", fcm.RIGID_BODY_MAX),
                         ("FCM_RIGID_PRECOND_DIAGONAL", fcm.RIGID_PRECOND_DIAGONAL),
-                        ("FCM_RIGID_PRECOND_BODY", fcm.RIGID_PRECOND_BODY)):
+                        ("FCM_RIGID_PRECOND_BODY", fcm.RIGID_PRECOND_BODY),
+                        ("FCM_STATUS_NONFINITE", fcm.STATUS_NONFINITE),
+                        ("FCM_STATUS_WAIT_TIMEOUT", fcm.STATUS_WAIT_TIMEOUT)):
         assert value == int(re.search(r"#define " + name + r" (\d+)", header).group(1)), name
