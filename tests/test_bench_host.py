@@ -70,3 +70,22 @@ def test_rod_suspension_parameters_follow_the_rules(n_rods, tol):
     assert pr["M_G"] == tune.support_points(pr["Sigma"], min(L_xy / Mx, L_z / Mz), tune.truncation_for(tune.GRID_SHARE * tol))
     assert 0 < pr["r_c"] <= 0.5 * L_z and pr["M_G"] <= min(24, Mz)
     assert pr["r_c"] >= tune.cutoff(pr["Sigma"], 0.5 * tol, torques=False) - 1e-9
+
+
+def test_reference_arm_prints_one_contract_line():
+    """`bench.py --impl reference` (the FP64 oracle on a bounded sample, host cores only) prints one JSON line
+    with the contract's keys, its own cpu_baseline and an e2e object with zero copy bytes."""
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip().startswith("{")]
+    assert len(lines) == 1, r.stdout
+    d = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["dtype"] == "f64" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
