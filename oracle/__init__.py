@@ -19,6 +19,10 @@ grid_fcm
     The grid algorithm of Section 2.1 (spread, FFT Stokes solve, trapezoidal
     interpolation), with either the FCM Gaussians (standard FCM) or the modified
     kernel of Section 3 plus the pairwise correction of Section 4 (fast FCM).
+fft
+    The unnormalised discrete Fourier transform and its inverse, written out
+    as a mixed-radix Cooley-Tukey recursion (prime lengths by the definition);
+    the grid Stokes solve and the Brownian grid noise use it.
 params
     Window rule, cutoff-radius rule and grid-support rule used by both the
     standard and the fast oracle.

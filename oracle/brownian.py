@@ -31,7 +31,8 @@ import math
 import numpy as np
 
 from . import closed_forms as cf
-from .grid_fcm import _as3, interpolate, neighbour_pairs, wavevectors, wrap
+from . import fft as offt
+from .grid_fcm import _as3, interpolate, neighbour_pairs, solve_keep_mask, wavevectors, wrap
 
 
 def grid_noise_velocity(xi, L, eta=1.0):
@@ -39,19 +40,13 @@ def grid_noise_velocity(xi, L, eta=1.0):
     M = np.array(xi.shape[1:], dtype=np.int64)
     kx, ky, kz = wavevectors(L, M)
     k2 = kx * kx + ky * ky + kz * kz
-    keep = k2 > 0
-    for d in range(3):
-        if M[d] % 2 == 0:
-            n = np.fft.fftfreq(int(M[d]), d=1.0 / M[d])
-            sl = [None, None, None]
-            sl[d] = slice(None)
-            keep = keep & ~np.broadcast_to((np.abs(n) == M[d] // 2)[tuple(sl)], keep.shape)
-    xh = np.stack([np.fft.fftn(xi[c]) for c in range(3)])
+    keep = solve_keep_mask(M)
+    xh = offt.dftn(xi)
     inv_k2 = np.where(keep, 1.0 / np.where(keep, k2, 1.0), 0.0)
     kdotx = (kx * xh[0] + ky * xh[1] + kz * xh[2]) * inv_k2
     inv_k = np.sqrt(inv_k2)
     uh = np.stack([xh[0] - kx * kdotx, xh[1] - ky * kdotx, xh[2] - kz * kdotx]) * (inv_k / math.sqrt(eta))
-    return np.stack([np.real(np.fft.ifftn(uh[c])) for c in range(3)])
+    return np.real(offt.idftn(uh))
 
 
 def brownian_grid(Y, xi, L, M_G, Sigma, Sigma_D, kT, a=1.0, eta=1.0):

@@ -13,6 +13,7 @@ Standard FCM (Section 2.1) and the grid part of fast FCM (Section 3.1, Section
 2. inverse Stokes operator L^-1 (Section 2.1 step 2): unnormalised FFT,
    u_k = (I - k^ k^) f_k / (eta k^2), inverse FFT divided by M; the k = 0 mode
    and every mode on a Nyquist plane (index M_i/2 of an even M_i) are set to 0;
+   the transforms are the oracle's own mixed-radix Cooley-Tukey DFT (``fft``);
 3. interpolate (J~ + N~) with the trapezoidal rule (Section 2.1 step 3):
        U_n = h^3 sum_g u(x_g) Delta~(x_g - Y_n; Sigma)
        W_n = h^3 sum_g Delta(x_g - Y_n; Sigma_D) (d_g x u(x_g)) / (2 Sigma_D^2),  d_g = x_g - Y_n
@@ -30,6 +31,7 @@ import math
 import numpy as np
 
 from . import closed_forms as cf
+from . import fft as offt
 from .params import window_start
 
 try:
@@ -115,11 +117,21 @@ def spread(Y, F, T, L, M, M_G, Sigma, Sigma_D, a=1.0, chunk=512, fp32_windows=Fa
 def wavevectors(L, M):
     """Spectral k per grid mode; index i maps to i if i <= M/2 else i - M."""
     L, M = _as3(L), _as3(M, np.int64)
-    ks = [2 * math.pi * np.fft.fftfreq(int(M[d]), d=1.0 / M[d]) / L[d] for d in range(3)]
-    for d in range(3):
-        if M[d] % 2 == 0:
-            ks[d][M[d] // 2] = abs(ks[d][M[d] // 2])
+    ks = [2 * math.pi * offt.mode_numbers(int(M[d])) / L[d] for d in range(3)]
     return np.meshgrid(*ks, indexing="ij")
+
+
+def solve_keep_mask(M):
+    """Modes kept by the Stokes solve: every mode but k = 0 and those on a Nyquist plane (index M_i/2
+    of an even M_i)."""
+    M = _as3(M, np.int64)
+    n = [offt.mode_numbers(int(M[d])) for d in range(3)]
+    nx, ny, nz = np.meshgrid(*n, indexing="ij")
+    keep = (nx != 0) | (ny != 0) | (nz != 0)
+    for d, nd in enumerate((nx, ny, nz)):
+        if M[d] % 2 == 0:
+            keep &= np.abs(nd) != M[d] // 2
+    return keep
 
 
 def stokes_solve(f, L, eta=1.0):
@@ -127,19 +139,12 @@ def stokes_solve(f, L, eta=1.0):
     M = np.array(f.shape[1:], dtype=np.int64)
     kx, ky, kz = wavevectors(L, M)
     k2 = kx * kx + ky * ky + kz * kz
-    keep = k2 > 0
-    for d, kk in enumerate((kx, ky, kz)):
-        if M[d] % 2 == 0:
-            n = np.fft.fftfreq(int(M[d]), d=1.0 / M[d])
-            sl = [None, None, None]
-            sl[d] = slice(None)
-            mask = np.broadcast_to((np.abs(n) == M[d] // 2)[tuple(sl)], keep.shape)
-            keep = keep & ~mask
-    fh = np.stack([np.fft.fftn(f[c]) for c in range(3)])
+    keep = solve_keep_mask(M)
+    fh = offt.dftn(f)
     inv_k2 = np.where(keep, 1.0 / np.where(keep, k2, 1.0), 0.0)
     kdotf = (kx * fh[0] + ky * fh[1] + kz * fh[2]) * inv_k2
     uh = np.stack([fh[0] - kx * kdotf, fh[1] - ky * kdotf, fh[2] - kz * kdotf]) * (inv_k2 / eta)
-    return np.stack([np.real(np.fft.ifftn(uh[c])) for c in range(3)])
+    return np.real(offt.idftn(uh))
 
 
 def interpolate(u, Y, L, M_G, Sigma, Sigma_D, a=1.0, chunk=512):
