@@ -67,6 +67,22 @@ def workload(name="c2", n=None, h_ref=None):
     return dict(name=name, n=n, phi=spec["phi"], L=L, M=M, h=h, Sigma=Sigma, M_G=MG, r_c=rc)
 
 
+def oracle_workload(name="c2", n=None, h_ref=None):
+    """The same workload with its parameters taken from the oracle's own rules (oracle/params.py), so
+    that the oracle's timed legs load nothing of the product (the two rules agree: tests/test_tune.py)."""
+    from oracle import params as op
+    from paper_2310_12651_gb300 import inputs
+    spec = WORKLOADS[name]
+    n = spec["n"] if n is None else n
+    L = inputs.box_edge(n, spec["phi"])
+    M = spec["grid"] if h_ref is None else max(8, int(round(L / h_ref)))
+    h = L / M
+    Sigma = spec["Sigma"]
+    MG = op.support_points(Sigma, h, TRUNC)
+    rc = op.cutoff_radius(Sigma, TOL, torques=True)
+    return dict(name=name, n=n, phi=spec["phi"], L=L, M=M, h=h, Sigma=Sigma, M_G=MG, r_c=rc)
+
+
 def describe(w, batch, precision="FP32"):
     return (f"uniform suspension, N={w['n']} spheres/system, phi={w['phi']:.0%} (L={w['L']:.2f}a), "
             f"{w['M']}^3 grid, Sigma={w['Sigma']}a, M_G={w['M_G']}, r_c={w['r_c']:.2f}a (1e-6 rule), "
@@ -164,21 +180,52 @@ def run_cpu_oracle(w, seed, torques=True):
     return time.perf_counter() - t
 
 
+def _oracle_worker(args):
+    w, seed = args
+    return run_cpu_oracle(w, seed)
+
+
 def cpu_baseline(name, target_s=15.0):
-    """The oracle timed on a bounded sample of the workload (same density, spacing, Sigma, M_G, r_c)."""
-    full = workload(name)
+    """The oracle timed on a bounded sample of the workload (same density, spacing, Sigma, M_G, r_c):
+    on one core, then on every host core at once (one independent sample system per core, as the
+    batched workload is independent systems; worker processes started with spawn, one BLAS thread
+    each)."""
+    import multiprocessing as mp
+    h_full = oracle_workload(name)["h"]
     n = 16384
-    w = workload(name, n=n, h_ref=full["h"])
+    w = oracle_workload(name, n=n, h_ref=h_full)
     secs = run_cpu_oracle(w, 2310126590)
     reps = 1
     while secs * (reps + 1) / reps < target_s and reps < 4:
         secs += run_cpu_oracle(w, 2310126590 + reps)
         reps += 1
-    return {"value": n * reps / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{reps} oracle apply(s) of {n} spheres at phi={w['phi']:.0%} (L={w['L']:.1f}a, {w['M']}^3, "
+    one = n * reps / secs
+    cores = len(os.sched_getaffinity(0))
+    value, used, wall = one, 1, secs
+    if cores > 1:
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in saved:
+            os.environ[k] = "1"
+        try:
+            with mp.get_context("spawn").Pool(cores) as pool:
+                pool.map(_oracle_worker, [(oracle_workload(name, n=512, h_ref=h_full), 1)] * cores)  # start-up
+                t0 = time.perf_counter()
+                pool.map(_oracle_worker, [(w, 2310126600 + k) for k in range(cores)])
+                wall = time.perf_counter() - t0
+            value, used = n * cores / wall, cores
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+    return {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": f"oracle applies of {n} spheres at phi={w['phi']:.0%} (L={w['L']:.1f}a, {w['M']}^3, "
                       f"h={w['h']:.3f}a, Sigma={w['Sigma']}a, M_G={w['M_G']}, r_c={w['r_c']:.2f}a), forces+torques, "
-                      f"FP64 numpy single thread, {secs:.1f} s",
-            "host_cores": len(os.sched_getaffinity(0))}
+                      f"FP64 numpy: {used} at once on {used} cores ({wall:.1f} s wall); one core alone "
+                      f"{reps} apply(s) in {secs:.1f} s",
+            "one_core": {"value": one, "cores": 1},
+            "host_cores": cores}
 
 
 # The paper's performance study (Section 5.2, Table 3): forces only, a/L = 1/400, eps = 1e-4, Sigma/dx = 1.00,
@@ -694,9 +741,8 @@ def serve_bench(device, requests=1024, loads=(0.5, 0.9), seed=2310126950):
 def reference_arm(args, world, rank):
     if rank != 0:
         return 0
-    full = workload(args.workload)
     n = 4096
-    w = workload(args.workload, n=n, h_ref=full["h"])
+    w = oracle_workload(args.workload, n=n, h_ref=oracle_workload(args.workload)["h"])
     for k in range(args.warmup):
         run_cpu_oracle(w, 2310126700 + k)
     t = 0.0

@@ -89,3 +89,27 @@ def test_reference_arm_prints_one_contract_line():
     assert d["impl"] == "reference" and d["dtype"] == "f64" and d["value"] > 0 and d["higher_is_better"] is True
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_oracle_legs_load_nothing_of_the_product():
+    """The reference arm and the CPU baseline take their parameters from oracle/params.py: after a
+    reference-arm run the process has neither mapped libfcm.so nor imported the binding or the tuner."""
+    import subprocess
+    code = (
+        "import sys, argparse, io, contextlib; sys.path.insert(0, %r)\n"
+        "import bench\n"
+        "a = argparse.Namespace(steps=1, warmup=0, gpus=1, workload='c2')\n"
+        "with contextlib.redirect_stdout(io.StringIO()):\n"
+        "    bench.reference_arm(a, 1, 0)\n"
+        "w = bench.oracle_workload('c2')\n"
+        "maps = open('/proc/self/maps').read()\n"
+        "assert 'libfcm' not in maps, 'libfcm.so mapped'\n"
+        "bad = [m for m in sys.modules if m.startswith('paper_2310_12651_gb300.') and m != 'paper_2310_12651_gb300.inputs']\n"
+        "assert not bad, bad\n"
+        "print('ok', w['M_G'], w['r_c'])\n" % ROOT)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    ok, mg, rc = r.stdout.split()
+    assert ok == "ok" and int(mg) == 14
+    import bench
+    assert abs(float(rc) - bench.workload("c2")["r_c"]) < 1e-6
