@@ -385,11 +385,16 @@ int fcm_server_destroy(fcm_server* s);
  *   pos, F, T (T may be NULL), U, W (W may be NULL): as for fcm_apply, on the
  *            current CUDA device
  * It allocates nothing: all scratch (about 7.7 MB) is one fixed file-scope
- * device array, held by every GPU that loads the library until the process
- * exits. The first call on a device looks up that array's address with the
- * device current; make it before any stream capture. Every call shares the
- * array and clears its counters first; calls whose work overlaps on the GPU
- * race on it. Sizes beyond the limits return FCM_ERR_ARG with a message. */
+ * device array, held by every CUDA context that loads the library's device
+ * code (normally one per GPU) until the process exits. With lazy module
+ * loading the context reserves it at the first call made in it: make that
+ * first call before a pool or arena takes the device's memory, and before any
+ * stream capture. Each call looks up the array's address in the context
+ * current at the time (addresses are per context; nothing is cached). Every
+ * call shares the array and clears its counters first; calls whose work
+ * overlaps on the GPU race on it. Non-finite positions are not reported (there
+ * is no status word to read; the result is then meaningless). Sizes beyond the
+ * limits return FCM_ERR_ARG with a message. */
 int fcm_pair_correction_noalloc(const fcm_params* p, int n, const void* pos, const void* F, const void* T,
                                 void* U, void* W, void* stream);
 

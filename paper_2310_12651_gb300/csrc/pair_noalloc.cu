@@ -9,16 +9,22 @@
 // pair kernels, and keeps every intermediate (sort keys, cell lists, sorted
 // particles, coefficient table) in one fixed-size file-scope device array.
 //
-// That array exists once per GPU that loads the library and stays allocated
-// until the process exits. Host code cannot use the array's name as a device
-// address, so the first call on each device looks the address up with
-// cudaGetSymbolAddress (with that device current) and caches it; make that
-// first call before any stream capture. Every call shares the array: the
-// counters are cleared at the start of each call, and two calls whose work
-// overlaps on the GPU (different streams, no ordering) race on it.
+// That array exists once per CUDA context that loads the library's device code
+// (normally one per GPU, the primary context) and stays allocated until the
+// process exits. With lazy module loading, the context reserves it at the first
+// call made in it: make that call before a pool or arena takes the device's
+// memory, and before any stream capture. Host code cannot use the array's name
+// as a device address; every call looks the address up with
+// cudaGetSymbolAddress in the context that is current at the time, so a
+// caller that switches contexts, or resets the device, gets the address valid
+// in the context it runs in (nothing is cached across calls). Every call
+// shares the array: the counters are cleared at the start of each call, and
+// two calls whose work overlaps on the GPU (different streams, no ordering)
+// race on it. Non-finite positions are clamped by the binning kernels as on
+// the handle path, but this entry point has no status word for the caller to
+// read: they go undetected and the result is meaningless.
 #include <cmath>
 #include <cstring>
-#include <mutex>
 #include <string>
 
 #include "../../include/fcm.h"
@@ -41,10 +47,6 @@ constexpr size_t kStatusBytes = kAlign;
 constexpr size_t kScratchBytes = kKeysBytes + kTileCountBytes + kCellCountBytes + kSortedBytes + kTableBytes + kStatusBytes;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_mutex;
-void* g_scratch_ptr[kMaxDevices];  // device address of g_noalloc_scratch per device, set on first use
 
 int fail(int code, const std::string& msg) { return record_error(code, msg.c_str()); }
 
@@ -69,20 +71,17 @@ __global__ void build_table_kernel(PairConsts<double> pd, double r_lo, double h,
   }
 }
 
-int scratch_for_device(int dev, unsigned char** out) {
-  if (dev < 0 || dev >= kMaxDevices) return fail(FCM_ERR_ARG, "device index out of range for the no-alloc path");
-  std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      cudaGetLastError();
-      return fail(FCM_ERR_CUDA, std::string("cudaGetSymbolAddress of the scratch array failed: ") +
-                                    cudaGetErrorString(e));
-    }
-    g_scratch_ptr[dev] = p;
+// Device address of g_noalloc_scratch in the current context (looked up on every call: an address
+// is valid only in the context it was taken in).
+int scratch_address(unsigned char** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    return fail(FCM_ERR_CUDA, std::string("cudaGetSymbolAddress of the scratch array failed: ") +
+                                  cudaGetErrorString(e));
   }
-  *out = static_cast<unsigned char*>(g_scratch_ptr[dev]);
+  *out = static_cast<unsigned char*>(p);
   return FCM_OK;
 }
 
@@ -137,13 +136,8 @@ extern "C" int fcm_pair_correction_noalloc(const fcm_params* p, int n, const voi
   if (n > 0 && (!pos || !F || !U)) return fail(FCM_ERR_ARG, "pos, F and U must be non-NULL when n > 0");
   if (n == 0) return FCM_OK;
 
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(FCM_ERR_CUDA, "no current CUDA device");
-  }
   unsigned char* base = nullptr;
-  int rc = scratch_for_device(dev, &base);
+  int rc = scratch_address(&base);
   if (rc != FCM_OK) return rc;
 
   BinBuffers b{};
