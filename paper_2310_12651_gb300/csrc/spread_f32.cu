@@ -246,6 +246,346 @@ __global__ void __launch_bounds__(rows_threads(MGT), 1) spread_rows_kernel(Geome
   }
 }
 
+// ---------------------------------------------------------------- pencil kernel
+//
+// spread_pencil_kernel (default for M_G <= 16 with 8-point tiles in x): one CTA walks a whole
+// x-pencil of binning tiles (all tiles with the same (y, z) tile index of one system; they are
+// contiguous in the tile-sorted order). Every thread owns one (y, z) row of the pencil's extended
+// (y, z) region and keeps a register row of EXT2 point pairs per component, anchored at the current
+// tile's x origin x0 = 8 s. Particles of tile s have window starts in [x0, x0 + 8), so once the walk
+// passes to tile s + 1 the points x0 .. x0 + 7 are complete for this pencil: they are added to the
+// grid (four pairs per component) and the register row shifts by four pairs. The x halo of one tile
+// is thus carried into the next tile in registers instead of being added to the grid, and only the
+// (y, z) halo is flushed with global reductions. A particle's row update is predicated (coefficients
+// zero outside its window): a warp skips a particle only when none of its rows is in the window, so
+// no lane diverges.
+//
+// The row update regroups the kernel's terms by their x profile. With G = g(dy) g(dz), the modified
+// kernel's polynomial P = A + B (dy^2 + dz^2), F' = nrm F and U' = tq T, a particle adds to its row
+//   f_c(x) += G alpha_c g(x) + G w_c(x),
+//   alpha = (F'x P + U'y dz - U'z dy, F'y P - U'x dz, F'z P + U'x dy),
+//   w = (B F'x d^2 g, B F'y d^2 g + U'z d g, B F'z d^2 g - U'y d g)      (d = x - Y_x, g = g(d))
+// for Sigma_D = Sigma: the x profiles g and w_c are staged once per particle, the row coefficients
+// G alpha_c and G once per particle-row, and a point takes six FMAs (three packed pairs per two
+// points). Forces only: f_c(x) += G F'_c (P g + B d^2 g). Sigma_D != Sigma keeps the torque terms on
+// their own profiles d g_D and g_D with the row factor H = tq g_D(dy) g_D(dz).
+
+enum { kPencilForces = 0, kPencilSameWidth = 1, kPencilTwoWidths = 2 };
+
+// Register pairs of a pencil row: window pairs start at pair ox / 2 with ox in [0, 8).
+__host__ __device__ constexpr int pencil_pairs(int MGT) { return row_pairs(MGT) + 3; }
+
+// Per-particle tables of the pencil kernel (one staged chunk).
+struct PencilTables {
+  float4* xa;   // [chunk][NP] {g, g', q, q'} (q = d^2 g; same width: q -> w_x = B F'x d^2 g), ' = next point
+  float4* xb;   // [chunk][NP] same width: {w_y, w_y', w_z, w_z'}
+  float4* yt;   // [chunk][MGT] {g, d, A + B d^2, g_D} along y
+  float4* zt;   // [chunk][MGT] {g, d, B d^2, g_D} along z
+  float4* pf;   // [chunk] F' = nrm F (two widths: F)
+  float4* pt;   // [chunk] U' = tq T (two widths: T)
+  int4* po;     // [chunk] (x offset in the tile, y and z window start in the region, tile step)
+  float* xk;    // two widths: [chunk][4 NK] d g_D along x, two pairs per float4
+  float* xd;    // two widths: [chunk][2 NP] g_D along x
+};
+
+template <int MGT>
+__device__ inline PencilTables pencil_tables(float4* sm) {
+  constexpr int NP = row_pairs(MGT), NK = (NP + 1) / 2;
+  PencilTables t;
+  t.xa = sm;
+  t.xb = t.xa + kRowsChunk * NP;
+  t.yt = t.xb + kRowsChunk * NP;
+  t.zt = t.yt + kRowsChunk * MGT;
+  t.pf = t.zt + kRowsChunk * MGT;
+  t.pt = t.pf + kRowsChunk;
+  t.po = reinterpret_cast<int4*>(t.pt + kRowsChunk);
+  t.xk = reinterpret_cast<float*>(t.po + kRowsChunk);
+  t.xd = t.xk + kRowsChunk * 4 * NK;
+  return t;
+}
+
+__host__ __device__ constexpr size_t pencil_tables_bytes(int MGT) {
+  return sizeof(float4) * (size_t)kRowsChunk * (2 * row_pairs(MGT) + 2 * MGT + 3 + (row_pairs(MGT) + 1) / 2) +
+         sizeof(float) * (size_t)kRowsChunk * 2 * row_pairs(MGT);
+}
+
+__device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
+
+template <int OXP, int NP, int EXT2, int MODE>
+__device__ __forceinline__ void pencil_row(const float4* __restrict__ xa, const float4* __restrict__ xb,
+                                           const float4* __restrict__ xk, const float2* __restrict__ xd,
+                                           float2 (&sx)[EXT2], float2 (&sy)[EXT2], float2 (&sz)[EXT2],
+                                           float c0, float c1, float c2, float c3, float c4, float c5,
+                                           float c6, float c7, float c8, float c9, float c10) {
+  static_assert(OXP + NP <= EXT2, "pair window beyond the row");
+  if (MODE == kPencilSameWidth) {   // c0 = G, c1..c3 = G alpha
+    const float2 G2 = dup2(c0), AX = dup2(c1), AY = dup2(c2), AZ = dup2(c3);
+#pragma unroll
+    for (int jp = 0; jp < NP; ++jp) {
+      const float4 p0 = xa[jp], p1 = xb[jp];
+      const float2 g2 = make_float2(p0.x, p0.y);
+      sx[OXP + jp] = __ffma2_rn(G2, make_float2(p0.z, p0.w), __ffma2_rn(AX, g2, sx[OXP + jp]));
+      sy[OXP + jp] = __ffma2_rn(G2, make_float2(p1.x, p1.y), __ffma2_rn(AY, g2, sy[OXP + jp]));
+      sz[OXP + jp] = __ffma2_rn(G2, make_float2(p1.z, p1.w), __ffma2_rn(AZ, g2, sz[OXP + jp]));
+    }
+  } else if (MODE == kPencilForces) {   // c0 = P, c1 = B, c2..c4 = G F'
+    const float2 P2 = dup2(c0), B2 = dup2(c1), FX = dup2(c2), FY = dup2(c3), FZ = dup2(c4);
+#pragma unroll
+    for (int jp = 0; jp < NP; ++jp) {
+      const float4 p0 = xa[jp];
+      const float2 w = __ffma2_rn(B2, make_float2(p0.z, p0.w), __fmul2_rn(P2, make_float2(p0.x, p0.y)));
+      sx[OXP + jp] = __ffma2_rn(FX, w, sx[OXP + jp]);
+      sy[OXP + jp] = __ffma2_rn(FY, w, sy[OXP + jp]);
+      sz[OXP + jp] = __ffma2_rn(FZ, w, sz[OXP + jp]);
+    }
+  } else {   // two widths: c0..c2 = a, c3..c5 = b, c6..c8 = c, c9 = ky, c10 = kz
+    const float2 AX = dup2(c0), AY = dup2(c1), AZ = dup2(c2), BX = dup2(c3), BY = dup2(c4), BZ = dup2(c5);
+    const float2 CX = dup2(c6), CY = dup2(c7), CZ = dup2(c8), KY = dup2(c9), KZ = dup2(c10);
+    float4 k4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int jp = 0; jp < NP; ++jp) {
+      const float4 p0 = xa[jp];
+      const float2 g2 = make_float2(p0.x, p0.y), q2 = make_float2(p0.z, p0.w);
+      if ((jp & 1) == 0) k4 = xk[jp >> 1];
+      const float2 k2 = (jp & 1) ? make_float2(k4.z, k4.w) : make_float2(k4.x, k4.y);
+      const float2 d2 = xd[jp];
+      float2 vx = __ffma2_rn(BX, q2, __ffma2_rn(AX, g2, sx[OXP + jp]));
+      float2 vy = __ffma2_rn(BY, q2, __ffma2_rn(AY, g2, sy[OXP + jp]));
+      float2 vz = __ffma2_rn(BZ, q2, __ffma2_rn(AZ, g2, sz[OXP + jp]));
+      vy = __ffma2_rn(KY, k2, vy);
+      vz = __ffma2_rn(KZ, k2, vz);
+      sx[OXP + jp] = __ffma2_rn(CX, d2, vx);
+      sy[OXP + jp] = __ffma2_rn(CY, d2, vy);
+      sz[OXP + jp] = __ffma2_rn(CZ, d2, vz);
+    }
+  }
+}
+
+// Adds pairs [k0, k1) of a register row to grid points x0 + 2k, x0 + 2k + 1 (wrapped into [0, M_x)):
+// 16-byte reductions where four points lie inside the row and the row holds whole float4s, scalar
+// atomics elsewhere; zeros are skipped.
+template <int EXT2>
+__device__ __forceinline__ void pencil_flush(int x0, int Mx, bool vec_rows, float* __restrict__ row,
+                                             const float2 (&s)[EXT2], int k0, int k1) {
+#pragma unroll
+  for (int k = 0; k < EXT2; k += 2) {
+    if (k < k0 || k >= k1) continue;
+    const int x = x0 + 2 * k;
+    const bool two = (k + 1 < EXT2) && (k + 1 < k1);
+    const float v0 = s[k].x, v1 = s[k].y;
+    const float v2 = two ? s[k + 1].x : 0.f, v3 = two ? s[k + 1].y : 0.f;
+    if (v0 == 0.f && v1 == 0.f && v2 == 0.f && v3 == 0.f) continue;
+    if (two && vec_rows && x + 3 < Mx) {
+      red_add_v4(row + x, v0, v1, v2, v3);
+    } else {
+      const float v[4] = {v0, v1, v2, v3};
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (v[e] != 0.f) atomicAdd(row + wrap_index(x + e, Mx), v[e]);
+    }
+  }
+}
+
+template <int EXT2>
+__device__ __forceinline__ void pencil_shift(float2 (&s)[EXT2]) {
+#pragma unroll
+  for (int k = 0; k < EXT2; ++k) s[k] = (k + 4 < EXT2) ? s[k + 4] : make_float2(0.f, 0.f);
+}
+
+template <int MGT, bool GUARD, int MODE>
+__global__ void __launch_bounds__(rows_threads(MGT), 1) spread_pencil_kernel(Geometry<float> g, KernelConsts<float> kc,
+                                                                          const float4* __restrict__ pos,
+                                                                          const float4* __restrict__ Fv,
+                                                                          const float4* __restrict__ Tv,
+                                                                          const int* __restrict__ tstart,
+                                                                          float* __restrict__ grid) {
+  constexpr int NP = row_pairs(MGT);
+  constexpr int NK = (NP + 1) / 2;
+  constexpr int EXT2 = pencil_pairs(MGT);
+  constexpr bool TORQUE = MODE != kPencilForces;
+  extern __shared__ float4 sm4[];
+  const int ntx = g.ntile[0], nty = g.ntile[1];
+  const int per = nty * g.ntile[2];
+  const int sys = blockIdx.x / per;
+  const int pc = blockIdx.x - sys * per;
+  const int t0 = sys * g.tiles_per + ntx * pc;          // tile (0, ty, tz) of the pencil
+  const int p_begin = tstart[t0], p_end = tstart[t0 + ntx];
+  if (p_begin >= p_end) return;
+  if (g.nsys > 1) grid += (size_t)sys * (size_t)g.grid_stride;
+  const int oy0 = (pc % nty) * g.tile[1], oz0 = (pc / nty) * g.tile[2];
+  const int MG = GUARD ? g.MG : MGT;
+  const int EY = g.tile[1] + MG - 1, EZ = g.tile[2] + MG - 1;
+  const int row = threadIdx.x;
+  const bool has_row = row < EY * EZ;
+  const int ez = has_row ? row / EY : 0;
+  const int ey = has_row ? row - ez * EY : 0;
+  float2 sx[EXT2], sy[EXT2], sz[EXT2];
+#pragma unroll
+  for (int k = 0; k < EXT2; ++k) {
+    sx[k] = make_float2(0.f, 0.f);
+    sy[k] = make_float2(0.f, 0.f);
+    sz[k] = make_float2(0.f, 0.f);
+  }
+  const PencilTables tb = pencil_tables<MGT>(sm4);
+  int cur = 0;   // tile step whose x origin anchors the register row
+
+  for (int base = p_begin; base < p_end; base += kRowsChunk) {
+    const int np = min(kRowsChunk, p_end - base);
+    __syncthreads();
+    // y and z profiles {g, d, A + B d^2 (y) or B d^2 (z), g_D}
+    for (int k = threadIdx.x; k < np * 2 * MGT; k += blockDim.x) {
+      const int q = k / (2 * MGT);
+      const int rem = k - q * 2 * MGT;
+      const int d = 1 + rem / MGT;
+      const int j = rem - (d - 1) * MGT;
+      const float4 y = pos[base + q];
+      const float yd = d == 1 ? y.y : y.z;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (j < MG) {
+        const float dd = (float)(window_start_d(g, d, yd) + j) * sel3(g.h, d) - yd;
+        const float gs = expf(-dd * dd * kc.inv2S2);
+        const float gd = MODE == kPencilTwoWidths ? expf(-dd * dd * kc.inv2SD2) : gs;
+        const float bq = kc.B * dd * dd;
+        v = make_float4(gs, dd, d == 1 ? kc.A + bq : bq, gd);
+      }
+      (d == 1 ? tb.yt : tb.zt)[q * MGT + j] = v;
+    }
+    // x profiles on even-aligned pairs: slot 2 jp + e holds window point j = 2 jp + e - (start & 1)
+    for (int k = threadIdx.x; k < np * 2 * NP; k += blockDim.x) {
+      const int q = k / (2 * NP);
+      const int slot = k - q * 2 * NP;
+      const float4 y = pos[base + q];
+      const int i0 = window_start_d(g, 0, y.x);
+      const int j = slot - (wrap_once(i0, g.M[0]) & 1);
+      float gs = 0.f, q2 = 0.f, dg = 0.f, gd = 0.f;
+      if (j >= 0 && j < MG) {
+        const float dd = (float)(i0 + j) * g.h[0] - y.x;
+        gs = expf(-dd * dd * kc.inv2S2);
+        gd = MODE == kPencilTwoWidths ? expf(-dd * dd * kc.inv2SD2) : gs;
+        q2 = dd * dd * gs;
+        dg = dd * gd;
+      }
+      float* ea = reinterpret_cast<float*>(tb.xa + (size_t)q * NP + (slot >> 1)) + (slot & 1);
+      ea[0] = gs;
+      if (MODE == kPencilSameWidth) {
+        const float4 f = Fv[base + q], t = Tv[base + q];
+        const float bn = kc.B * kc.nrm;
+        float* eb = reinterpret_cast<float*>(tb.xb + (size_t)q * NP + (slot >> 1)) + (slot & 1);
+        ea[2] = bn * f.x * q2;
+        eb[0] = fmaf(bn * f.y, q2, kc.tq * t.z * dg);
+        eb[2] = fmaf(bn * f.z, q2, -kc.tq * t.y * dg);
+      } else {
+        ea[2] = q2;
+      }
+      if (MODE == kPencilTwoWidths) {
+        tb.xk[(size_t)q * 4 * NK + slot] = dg;
+        tb.xd[(size_t)q * 2 * NP + slot] = gd;
+      }
+    }
+    for (int q = threadIdx.x; q < np; q += blockDim.x) {
+      const float4 y = pos[base + q];
+      const int3 i0 = window_starts(g, y);
+      const int wx = wrap_once(i0.x, g.M[0]);
+      const int step = min(max(wx >> 3, 0), ntx - 1);
+      int4 off;
+      off.x = min(max(wx - 8 * step, 0), 7);
+      off.y = min(max(wrap_once(i0.y, g.M[1]) - oy0, 0), g.tile[1] - 1);
+      off.z = min(max(wrap_once(i0.z, g.M[2]) - oz0, 0), g.tile[2] - 1);
+      off.w = step;
+      tb.po[q] = off;
+      const float4 f = Fv[base + q];
+      const float4 t = TORQUE ? Tv[base + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+      if (MODE == kPencilTwoWidths) {
+        tb.pf[q] = f;
+        tb.pt[q] = t;
+      } else {
+        tb.pf[q] = make_float4(kc.nrm * f.x, kc.nrm * f.y, kc.nrm * f.z, 0.f);
+        tb.pt[q] = make_float4(kc.tq * t.x, kc.tq * t.y, kc.tq * t.z, 0.f);
+      }
+    }
+    __syncthreads();
+    for (int q = 0; q < np; ++q) {
+      const int4 off = tb.po[q];
+      // the walk reaches the particle's tile: complete points of the passed tiles go to the grid
+      while (cur < off.w) {
+        if (has_row) {
+          const size_t Mtot = (size_t)g.M[0] * g.M[1] * g.M[2];
+          float* r0 = grid + ((size_t)wrap_index(oz0 + ez, g.M[2]) * g.M[1] + wrap_index(oy0 + ey, g.M[1])) * g.M[0];
+          const bool vec_rows = (g.M[0] & 3) == 0;
+          pencil_flush<EXT2>(8 * cur, g.M[0], vec_rows, r0, sx, 0, 4);
+          pencil_flush<EXT2>(8 * cur, g.M[0], vec_rows, r0 + Mtot, sy, 0, 4);
+          pencil_flush<EXT2>(8 * cur, g.M[0], vec_rows, r0 + 2 * Mtot, sz, 0, 4);
+        }
+        pencil_shift<EXT2>(sx);
+        pencil_shift<EXT2>(sy);
+        pencil_shift<EXT2>(sz);
+        ++cur;
+      }
+      const int jy = ey - off.y, jz = ez - off.z;
+      const bool in = has_row && (unsigned)jy < (unsigned)MG && (unsigned)jz < (unsigned)MG;
+      if (!__any_sync(kFullMask32, in)) continue;
+      const float4 yv = tb.yt[q * MGT + (in ? jy : 0)];
+      const float4 zv = tb.zt[q * MGT + (in ? jz : 0)];
+      const float4 f = tb.pf[q];
+      const float P = yv.z + zv.z;
+      float c[11];
+      if (MODE == kPencilSameWidth) {
+        const float4 u = tb.pt[q];
+        const float G = in ? yv.x * zv.x : 0.f;
+        const float dy = yv.y, dz = zv.y;
+        c[0] = G;
+        c[1] = G * fmaf(f.x, P, fmaf(u.y, dz, -u.z * dy));
+        c[2] = G * fmaf(f.y, P, -u.x * dz);
+        c[3] = G * fmaf(f.z, P, u.x * dy);
+        for (int k = 4; k < 11; ++k) c[k] = 0.f;
+      } else if (MODE == kPencilForces) {
+        const float G = in ? yv.x * zv.x : 0.f;
+        c[0] = P;
+        c[1] = kc.B;
+        c[2] = G * f.x;
+        c[3] = G * f.y;
+        c[4] = G * f.z;
+        for (int k = 5; k < 11; ++k) c[k] = 0.f;
+      } else {
+        const float4 tq = tb.pt[q];
+        const float G = in ? kc.nrm * yv.x * zv.x : 0.f;
+        const float GQ = G * P, GB = G * kc.B;
+        const float H = in ? kc.tq * yv.w * zv.w : 0.f;
+        const float dy = yv.y, dz = zv.y;
+        c[0] = f.x * GQ; c[1] = f.y * GQ; c[2] = f.z * GQ;
+        c[3] = f.x * GB; c[4] = f.y * GB; c[5] = f.z * GB;
+        c[6] = H * (tq.y * dz - tq.z * dy);
+        c[7] = -H * tq.x * dz;
+        c[8] = H * tq.x * dy;
+        c[9] = H * tq.z;
+        c[10] = -H * tq.y;
+      }
+      const float4* xa = tb.xa + (size_t)q * NP;
+      const float4* xb = tb.xb + (size_t)q * NP;
+      const float4* xk = reinterpret_cast<const float4*>(tb.xk + (size_t)q * 4 * NK);
+      const float2* xd = reinterpret_cast<const float2*>(tb.xd + (size_t)q * 2 * NP);
+#define FCM_PENCIL_CASE(OXP)                                                                                    \
+  case OXP:                                                                                                     \
+    pencil_row<OXP, NP, EXT2, MODE>(xa, xb, xk, xd, sx, sy, sz, c[0], c[1], c[2], c[3], c[4], c[5], c[6], c[7], \
+                                    c[8], c[9], c[10]);                                                         \
+    break;
+      switch (off.x >> 1) {
+        FCM_PENCIL_CASE(0) FCM_PENCIL_CASE(1) FCM_PENCIL_CASE(2) FCM_PENCIL_CASE(3)
+        default: break;
+      }
+#undef FCM_PENCIL_CASE
+    }
+  }
+  if (has_row) {   // the last tile reached: every pair of the register row, x from 8 cur on
+    const size_t Mtot = (size_t)g.M[0] * g.M[1] * g.M[2];
+    float* r0 = grid + ((size_t)wrap_index(oz0 + ez, g.M[2]) * g.M[1] + wrap_index(oy0 + ey, g.M[1])) * g.M[0];
+    const bool vec_rows = (g.M[0] & 3) == 0;
+    pencil_flush<EXT2>(8 * cur, g.M[0], vec_rows, r0, sx, 0, EXT2);
+    pencil_flush<EXT2>(8 * cur, g.M[0], vec_rows, r0 + Mtot, sy, 0, EXT2);
+    pencil_flush<EXT2>(8 * cur, g.M[0], vec_rows, r0 + 2 * Mtot, sz, 0, EXT2);
+  }
+}
+
 // ---------------------------------------------------------------- atomic kernel
 
 template <int MGT, bool GUARD, bool TORQUE, bool SAMEW>
@@ -377,11 +717,24 @@ static bool rows_selected(const Geometry<float>& g, int spread_kernel) {
   return spread_uses_rows(g.tile, g.MG);
 }
 
+template <int MGT, bool GUARD, int MODE>
+static void pencil_variant(const Geometry<float>& g, const KernelConsts<float>& kc, const BinBuffers& b, float* grid,
+                           cudaStream_t s) {
+  const size_t smem = pencil_tables_bytes(MGT);
+  const int threads = (((g.tile[1] + g.MG - 1) * (g.tile[2] + g.MG - 1) + 31) / 32) * 32;
+  const int nsys = g.nsys > 1 ? g.nsys : 1;
+  const int blocks = nsys * g.ntile[1] * g.ntile[2];
+  auto k = spread_pencil_kernel<MGT, GUARD, MODE>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k<<<blocks, threads, smem, s>>>(g, kc, (const float4*)b.t_pos, (const float4*)b.t_F, (const float4*)b.t_T,
+                                  b.tile_start, grid);
+}
+
 size_t spread_smem_bytes(const int tile[3], int MG) {
   if (!spread_uses_rows(tile, MG)) return tile_smem_bytes(tile, MG);
-  const size_t tab = row_tables_bytes(rows_mgt(MG));
+  const size_t tab = std::max(row_tables_bytes(rows_mgt(MG)), pencil_tables_bytes(rows_mgt(MG)));
   const size_t ext = tile_smem_bytes(tile, MG);
-  return tab > ext ? tab : ext;  // either kernel may be selected for this tile
+  return tab > ext ? tab : ext;  // any of the kernels may be selected for this tile
 }
 
 // Row-stationary spread over pairs of x-adjacent binning tiles (16-point rows).
@@ -422,6 +775,13 @@ void launch_spread_f32(const Geometry<float>& g, const KernelConsts<float>& kc, 
                        const BinBuffers& b, float* grid, cudaStream_t s, long long* launches) {
   if (spread_kernel == 3 && spread_mma_eligible(g.tile, g.MG)) {
     launch_spread_mma(g, kc, torque, b, grid, s);
+  } else if (rows_selected(g, spread_kernel) && spread_kernel != 1) {
+#define PENCIL_CALL(MGT, GUARD)                                                            \
+  if (!torque) pencil_variant<MGT, GUARD, kPencilForces>(g, kc, b, grid, s);              \
+  else if (kc.same_width) pencil_variant<MGT, GUARD, kPencilSameWidth>(g, kc, b, grid, s); \
+  else pencil_variant<MGT, GUARD, kPencilTwoWidths>(g, kc, b, grid, s);
+    FCM_DISPATCH_ROWS(g.MG, PENCIL_CALL)
+#undef PENCIL_CALL
   } else if (rows_selected(g, spread_kernel)) {
 #define ROWS_CALL(MGT, GUARD)                                                              \
   if (!torque) rows_variant<MGT, GUARD, false, true>(g, kc, b, grid, s);                  \

@@ -59,9 +59,10 @@ def test_fp32_torques_several_tiles(fcm, Sigma, M):
     assert_parity(W, Wo, FP32_TOL, f"W fp32 Sigma={Sigma}")
 
 
-@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("kernel", [0, 1, 2])
 def test_fp32_both_spread_kernels(fcm, kernel):
-    """Row-stationary (1) and shared-atomic (2) spread kernels give the same product."""
+    """Pencil (0, the default), row-stationary per tile pair (1) and shared-atomic (2) spread kernels give
+    the same product."""
     torch = torch_cuda()
     s = suspension(5000, 0.05, 48, 2.0, 1e-6, 66)
     p = fcm.make_params(s.L, s.M, s.Sigma, s.r_c, s.M_G, s.n, fcm.FCM_FP32, spread_kernel=kernel)
@@ -110,6 +111,38 @@ def test_spread_grid_matches_oracle(fcm, precision):
     got = grid.double().cpu().numpy().reshape(3, s.M, s.M, s.M).transpose(0, 3, 2, 1)  # -> [c][x][y][z]
     ref = og.spread(rounded(s.Y, prec), rounded(s.F, prec), rounded(s.T, prec), s.L, s.M, s.M_G, s.Sigma, s.Sigma)
     assert_parity(got, ref, FP32_TOL if precision == "fp32" else FP64_TOL, f"spread grid {precision}")
+
+
+@pytest.mark.parametrize("M, Sigma, c_trunc, torques, sigma_d", [
+    (42, 2.0, 4.7, True, 0.0),     # M_G = 14, M_x not a multiple of 4: scalar flushes; ragged last tile of 2 points
+    (44, 1.5, 4.8, True, 0.0),     # M_G = 12, ragged last tile of 4 points
+    (40, 2.0, 4.0, False, 0.0),    # forces only, M_G = 12
+    (36, 2.0, 5.2, True, 0.0),     # M_G = 16: (8, 4, 4) tiles
+    (32, 1.2, 4.8, True, 1.5),     # Sigma_D != Sigma, M_G = 10 at h = 1.1
+    (16, 2.0, 4.8, True, 0.0),     # M_G = 14: the extended row (21 points) wraps past M_x = 16
+])
+def test_pencil_spread_grid_matches_oracle(fcm, M, Sigma, c_trunc, torques, sigma_d):
+    """The pencil spread's force density point by point: ragged and wrapping rows, the M_G variants, forces
+    only and a torque width different from Sigma."""
+    torch = torch_cuda()
+    n = max(200, int(0.05 * (M * 1.37) ** 3 / 4.19))
+    s = suspension(n, 0.05, M, Sigma, 1e-6, 460 + M, torques=torques, c_trunc=c_trunc)
+    s.Sigma_D = sigma_d
+    SD = sigma_d if sigma_d else Sigma
+    p = fcm.make_params(s.L, s.M, s.Sigma, s.r_c, s.M_G, s.n, fcm.FCM_FP32, Sigma_D=sigma_d, spread_kernel=0)
+    with fcm.Handle(p) as h:
+        pos = torch.as_tensor(s.Y, dtype=torch.float32, device="cuda")
+        F = torch.as_tensor(s.F, dtype=torch.float32, device="cuda")
+        T = torch.as_tensor(s.T, dtype=torch.float32, device="cuda") if torques else None
+        h.spread(s.n, pos, F, T, torch.cuda.current_stream().cuda_stream)
+        grid = torch.empty(3 * s.M ** 3, dtype=torch.float32, device="cuda")
+        h.copy_grid(grid, torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+    got = grid.double().cpu().numpy().reshape(3, s.M, s.M, s.M).transpose(0, 3, 2, 1)
+    T64 = rounded(s.T, fcm.FCM_FP32) if torques else None
+    ref = og.spread(rounded(s.Y, fcm.FCM_FP32), rounded(s.F, fcm.FCM_FP32), T64, s.L, s.M, s.M_G, s.Sigma, SD,
+                    fp32_windows=True)
+    assert_parity(got, ref, FP32_TOL, f"pencil spread grid M={M} M_G={s.M_G}")
 
 
 # ---------------------------------------------------------------- edge cases and degenerate cases
