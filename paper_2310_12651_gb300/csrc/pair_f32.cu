@@ -12,12 +12,13 @@
 //
 // GB300 decomposition: one CTA per pair cell stages the candidates of the 27
 // neighbour cells in shared memory; a warp takes one particle n at a time.
-// Lanes test 32 candidates at a time; hits are compacted with a ballot into a
-// per-warp shared-memory queue, and the correction is evaluated when 32 hits
-// are queued, so that work runs with every lane busy although only ~15% of
-// candidates are within r_c. Per-lane sums are compensated (Neumaier), the
-// warp reduction is a tree, and the per-particle totals over candidate chunks
-// are compensated again.
+// Lanes test 32 candidates at a time; the staged slots of hits are compacted
+// with a ballot into a per-warp shared-memory queue, and the correction is
+// evaluated when 32 hits are queued (each lane recomputes its pair's
+// separation from the staged position), so that work runs with every lane busy
+// although only ~15% of candidates are within r_c. Per-lane sums are
+// compensated (Kahan), the warp reduction is a tree, and the per-particle
+// totals over candidate chunks are compensated again (Neumaier).
 #include "fcm_internal.cuh"
 
 namespace fcm {
@@ -26,7 +27,7 @@ constexpr unsigned kFullMask = 0xffffffffu;
 constexpr int kQueue = 64;
 
 // Compensated (Kahan) running sum: c carries the low-order part lost by s.
-struct Neu {
+struct Kahan {
   float s, c;
   __device__ inline void add(float v) {
     const float y = v - c;
@@ -45,7 +46,7 @@ __device__ inline float min_image(float d, float L) {
 
 template <bool TORQUE>
 __device__ inline void eval_pair(const PairConsts<float>& pc, const PairTable& tab, float4 dq, float4 Fj, float4 Tj,
-                                 Neu* u, Neu* w) {
+                                 Kahan* u, Kahan* w) {
   float al, bt, cr, gm, dl;
   pair_coeffs_table(dq.w, pc, tab, al, bt, cr, gm, dl);
   const float dx = dq.x, dy = dq.y, dz = dq.z;
@@ -78,16 +79,15 @@ __device__ inline void eval_pair(const PairConsts<float>& pc, const PairTable& t
 // loads instead of L2 traffic repeated for every particle of the cell.
 
 constexpr int kCellWarps = 8;
-constexpr int kCandChunk = 1024;
-static_assert(kCandChunk % 64 == 0, "candidate chunks are padded to whole 64-candidate passes");
+constexpr int kCandChunk = 1280;   // above the 27-cell candidate count of the 5% suspension (about 1,025)
+static_assert(kCandChunk % 32 == 0, "candidate chunks are padded to whole 32-candidate passes");
 constexpr int kIBatch = 128;
 constexpr int kMaxPieces = 18;
 
 template <bool TORQUE>
 constexpr size_t cell_kernel_smem() {
   return sizeof(float4) * (size_t)kCandChunk * (TORQUE ? 3 : 2) + sizeof(float) * 12 * kIBatch +
-         sizeof(float4) * kCellWarps * kQueue + sizeof(int) * kCellWarps * kQueue + sizeof(int) * 64 +
-         sizeof(float4) * kMaxPieces;
+         sizeof(int) * kCellWarps * kQueue + sizeof(int) * 64 + sizeof(float4) * kMaxPieces;
 }
 
 __device__ inline void neu_add(float* s, float* c, float v) {
@@ -110,8 +110,7 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) pair_cell_kernel(Geometry<
   float4* sF = spos + kCandChunk;
   float4* sT = sF + kCandChunk;
   float* acc = reinterpret_cast<float*>(TORQUE ? sT + kCandChunk : sT);   // [kIBatch][12]
-  float4* qd = reinterpret_cast<float4*>(acc + 12 * kIBatch);               // [warps][kQueue]
-  int* qj = reinterpret_cast<int*>(qd + kCellWarps * kQueue);               // [warps][kQueue]
+  int* qj = reinterpret_cast<int*>(acc + 12 * kIBatch);                     // [warps][kQueue]
   int* meta = qj + kCellWarps * kQueue;                                     // pieces: source start, prefix
   float4* pshift = reinterpret_cast<float4*>(meta + 64);                    // periodic image shift per piece
 
@@ -156,7 +155,6 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) pair_cell_kernel(Geometry<
   const int npieces = meta[63];
   const int total = meta[2 * npieces + 1];
   const unsigned lt = (1u << lane) - 1u;
-  float4* myqd = qd + warp * kQueue;
   int* myqj = qj + warp * kQueue;
 
   for (int ib = i_begin; ib < i_end; ib += kIBatch) {
@@ -177,56 +175,48 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) pair_cell_kernel(Geometry<
           if (TORQUE) sT[lo - cb + k] = cT[src + k];
         }
       }
-      // pad to whole 64-candidate passes with far-away dummies (index -1): no bounds test in the loop
-      const int ncp = (nc + 63) & ~63;
+      // pad to whole 32-candidate passes with far-away dummies (index -1): no bounds test in the loop
+      const int ncp = (nc + 31) & ~31;
       for (int k = nc + threadIdx.x; k < ncp; k += blockDim.x)
         spos[k] = make_float4(1e18f, 1e18f, 1e18f, __int_as_float(-1));
       __syncthreads();
       for (int il = warp; il < ni; il += kCellWarps) {
         const float4 yi = cpos[ib + il];
         const int self = __float_as_int(yi.w);
-        Neu u[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-        Neu w[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-        int qh = 0, qn = 0;
-        for (int base = 0; base < ncp; base += 64) {
-          // two warp passes per iteration: both candidates' tests are issued before either push
-          float4 dq[2];
-          bool hit[2];
-#pragma unroll
-          for (int k = 0; k < 2; ++k) {
-            const float4 yj = spos[base + 32 * k + lane];
-            dq[k].x = SHIFT ? yi.x - yj.x : min_image(yi.x - yj.x, g.L[0]);
-            dq[k].y = SHIFT ? yi.y - yj.y : min_image(yi.y - yj.y, g.L[1]);
-            dq[k].z = SHIFT ? yi.z - yj.z : min_image(yi.z - yj.z, g.L[2]);
-            dq[k].w = dq[k].x * dq[k].x + dq[k].y * dq[k].y + dq[k].z * dq[k].z;
-            hit[k] = dq[k].w < pc.rc2 && __float_as_int(yj.w) != self;
-          }
-#pragma unroll
-          for (int k = 0; k < 2; ++k) {
-            const unsigned m = __ballot_sync(kFullMask, hit[k]);
-            if (hit[k]) {
-              const int slot = (qh + qn + __popc(m & lt)) & (kQueue - 1);
-              myqd[slot] = dq[k];
-              myqj[slot] = base + 32 * k + lane;
-            }
-            qn += __popc(m);
+        Kahan u[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        Kahan w[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        // one queued hit: the separation is recomputed from the staged position
+        auto eval_slot = [&](int jj) {
+          const float4 yj = spos[jj];
+          float4 dq;
+          dq.x = SHIFT ? yi.x - yj.x : min_image(yi.x - yj.x, g.L[0]);
+          dq.y = SHIFT ? yi.y - yj.y : min_image(yi.y - yj.y, g.L[1]);
+          dq.z = SHIFT ? yi.z - yj.z : min_image(yi.z - yj.z, g.L[2]);
+          dq.w = fmaf(dq.x, dq.x, fmaf(dq.y, dq.y, dq.z * dq.z));
+          eval_pair<TORQUE>(pc, tab, dq, sF[jj], TORQUE ? sT[jj] : make_float4(0.f, 0.f, 0.f, 0.f), u, w);
+        };
+        int qn = 0;   // queued hits (the same in every lane); the queue starts at slot 0
+        for (int base = 0; base < ncp; base += 32) {
+          const float4 yj = spos[base + lane];
+          const float dx = SHIFT ? yi.x - yj.x : min_image(yi.x - yj.x, g.L[0]);
+          const float dy = SHIFT ? yi.y - yj.y : min_image(yi.y - yj.y, g.L[1]);
+          const float dz = SHIFT ? yi.z - yj.z : min_image(yi.z - yj.z, g.L[2]);
+          const bool hit = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < pc.rc2 && __float_as_int(yj.w) != self;
+          const unsigned m = __ballot_sync(kFullMask, hit);
+          if (m == 0u) continue;
+          if (hit) myqj[qn + __popc(m & lt)] = base + lane;   // qn < 32 here, so the slot is < 64
+          qn += __popc(m);
+          if (qn >= 32) {
             __syncwarp();
-            if (qn >= 32) {
-              const int slot = (qh + lane) & (kQueue - 1);
-              const int jj = myqj[slot];
-              eval_pair<TORQUE>(pc, tab, myqd[slot], sF[jj], TORQUE ? sT[jj] : make_float4(0.f, 0.f, 0.f, 0.f), u,
-                                w);
-              qh = (qh + 32) & (kQueue - 1);
-              qn -= 32;
-              __syncwarp();
-            }
+            eval_slot(myqj[lane]);
+            __syncwarp();
+            if (lane < qn - 32) myqj[lane] = myqj[32 + lane];   // the overflow moves to the front
+            qn -= 32;
+            __syncwarp();
           }
         }
-        if (lane < qn) {
-          const int slot = (qh + lane) & (kQueue - 1);
-          const int jj = myqj[slot];
-          eval_pair<TORQUE>(pc, tab, myqd[slot], sF[jj], TORQUE ? sT[jj] : make_float4(0.f, 0.f, 0.f, 0.f), u, w);
-        }
+        __syncwarp();
+        if (lane < qn) eval_slot(myqj[lane]);
         __syncwarp();
         float r[6] = {u[0].value(), u[1].value(), u[2].value(), w[0].value(), w[1].value(), w[2].value()};
 #pragma unroll
