@@ -54,8 +54,9 @@ typedef enum fcm_status {
 } fcm_status;
 
 typedef enum fcm_precision {
-  FCM_FP32 = 0,  /* float I/O; tiled spread/gather, FP32 FFT, FP32 pair closed form */
-                 /* with the small-r series, compensated per-particle pair sums      */
+  FCM_FP32 = 0,  /* float I/O; tiled spread/gather, FP32 FFT; pair corrections from  */
+                 /* piecewise cubics fitted in FP64 to the closed forms, a Taylor    */
+                 /* series below sigma/2, compensated per-particle pair sums         */
   FCM_FP64 = 1   /* double I/O; the plain path: global FP64 atomics, FP64 FFT        */
 } fcm_precision;
 
@@ -83,23 +84,34 @@ typedef struct fcm_params {
 
 typedef struct fcm_handle fcm_handle;
 
-/* Library and ABI version, major*10000 + minor*100 + patch. */
+/* Library and ABI version, major*10000 + minor*100 + patch. (No counterpart
+ * in the paper.) */
 int fcm_version(void);
 
-/* Fills p with a = eta = 1, Sigma_D = 0, tile = 0 and precision FCM_FP32; the
+/* Fills p with a = eta = 1 (the paper keeps eta symbolic), Sigma_D = 0 (the end
+ * of Section 3.4 sets Sigma_D = Sigma), tile = 0 and precision FCM_FP32; the
  * caller sets L, M, Sigma, r_c, M_G and max_n. Returns FCM_ERR_ARG if p is NULL. */
 int fcm_params_default(fcm_params* p);
 
 /* Validates p and builds a handle on CUDA device `device`: workspace for max_n
- * particles, the grid, cuFFT plans and an internal stream. On failure *out is
- * NULL and nothing is leaked. Synchronous. */
+ * particles, the grid, cuFFT plans and an internal stream. The parameters are
+ * those the paper sets per system: box and grid (Section 2.1), the modified
+ * widths Sigma, Sigma_D (Section 3.1, end of Section 3.4), the cutoff r_c and
+ * the cell list it implies (Section 4, step 1) and the grid support M_G
+ * (Section 5.1, Table 1). On failure *out is NULL and nothing is leaked.
+ * Synchronous. */
 int fcm_create(const fcm_params* p, int device, fcm_handle** out);
 
 /* Releases everything fcm_create allocated; NULL is a no-op. Synchronises the
- * handle's device. */
+ * handle's device. (Resource management: no counterpart in the paper.) */
 int fcm_destroy(fcm_handle* h);
 
-/* (U, W) = M (F, T) for n particles (0 <= n <= max_n).
+/* (U, W) = M (F, T) for n particles (0 <= n <= max_n): the fast FCM algorithm
+ * of Section 4 (steps 1-6): hashing and sort, spread with the modified kernels
+ * (eq. force_kernel_mod, eq. torque_kernel_mod), the Stokes solve by FFT
+ * (Section 2.1, step 2), interpolation (eq. avg_particle_vel_mod,
+ * eq. avg_particle_rot_mod) and the pairwise and self corrections
+ * (eq. correction_VF, eq. correction_WF, eq. correction_WT, Appendix B).
  *   pos : (n, 3) positions                       [device, read]
  *   F   : (n, 3) forces                          [device, read]
  *   T   : (n, 3) torques, or NULL for zero       [device, read]
@@ -119,7 +131,9 @@ enum {
 };
 
 /* fcm_apply restricted to the stages in `stages`; the outputs hold the sum of
- * the selected parts. Used to check each part of the product on its own. */
+ * the selected parts: the grid part M~ and the correction M - M~ of the
+ * splitting M = M~ + (M - M~) (Section 3.2, Section 3.4). Used to check each
+ * part of the product on its own. */
 int fcm_apply_stages(fcm_handle* h, int n, const void* pos, const void* F, const void* T,
                      void* U, void* W, int stages, void* stream);
 
@@ -241,17 +255,20 @@ int fcm_batch_apply(fcm_handle* h, int n_sys, const int* offsets, const void* po
 int fcm_batch_apply_stages(fcm_handle* h, int n_sys, const int* offsets, const void* pos, const void* F,
                            const void* T, void* U, void* W, int stages, void* stream);
 
-/* max_systems of the handle (1 for fcm_create), 0 for NULL. */
+/* max_systems of the handle (1 for fcm_create), 0 for NULL. (No counterpart in
+ * the paper.) */
 int fcm_max_systems(const fcm_handle* h);
 
-/* Copies the handle's real grid (3 components, layout [c][z][y][x], x fastest,
+/* Copies the handle's real grid (the periodic grid of Section 2.1; 3 components,
+ * layout [c][z][y][x], x fastest,
  * M_x*M_y*M_z values per component, the handle's precision) to device memory
  * `dst`. After fcm_apply_stages(FCM_STAGE_GRID) it holds the grid velocity u;
  * after fcm_spread it holds the spread force density f. A batch handle copies
  * the grid of system 0. */
 int fcm_copy_grid(fcm_handle* h, void* dst, void* stream);
 
-/* Sort and spread only: afterwards the grid holds f (Section 4, steps 1-3). */
+/* Sort and spread only: afterwards the grid holds f (Section 4, steps 1-3;
+ * eq. force_kernel_mod and eq. torque_kernel_mod). */
 int fcm_spread(fcm_handle* h, int n, const void* pos, const void* F, const void* T, void* stream);
 
 /* Bits of the device status word that fcm_check reports. */
@@ -259,13 +276,16 @@ int fcm_spread(fcm_handle* h, int n, const void* pos, const void* F, const void*
 #define FCM_STATUS_WAIT_TIMEOUT 2 /* a bounded wait inside a kernel ran out: that pass's result */
                                   /* is incomplete                                              */
 
-/* Waits (bounded by timeout_ms, polling) for all work the handle enqueued on
+/* Failure detection, no counterpart in the paper. Waits (bounded by
+ * timeout_ms, polling) for all work the handle enqueued on
  * `stream`, then reads and clears the device status word into *flags
  * (FCM_STATUS_* bits). Returns FCM_ERR_TIMEOUT if the wait ran out,
  * FCM_ERR_INPUT if flags != 0. */
 int fcm_check(fcm_handle* h, void* stream, int timeout_ms, int* flags);
 
-/* Per-stage timing with CUDA events recorded on the stream each stage runs on.
+/* Per-stage timing with CUDA events recorded on the stream each stage runs on
+ * (the stages of the algorithm of Section 4; the paper times whole applies,
+ * Section 5.2).
  * Stage ids: 0 binning (key/count, scan, scatter kernels), 1 spread kernel
  * (the grid zero-fill before it is not included), 2 FFT + projection +
  * inverse FFT, 3 gather kernel, 4 pair-correction kernel (side stream),
@@ -277,14 +297,18 @@ int fcm_set_timing(fcm_handle* h, int enable);
  * resets the sums. ms and counts must hold FCM_NUM_STAGES entries. */
 int fcm_read_timing(fcm_handle* h, double* ms, long long* counts);
 
-/* Number of kernels of this library launched through the handle so far
+/* (No counterpart in the paper.) Number of kernels of this library launched
+ * through the handle so far
  * (library kernels only; cuFFT's own kernels are not counted). */
 long long fcm_launch_count(const fcm_handle* h);
 
-/* Device bytes the handle holds (workspace, grid, spectrum, cuFFT work area). */
+/* Device bytes the handle holds (workspace, grid, spectrum, cuFFT work area);
+ * the paper's memory estimate for the grid is in Section 2.1. */
 size_t fcm_workspace_bytes(const fcm_handle* h);
 
-/* Parameter rule of the autotuner: the smallest r with every normalised block
+/* Parameter rule of the autotuner, the tolerance-related cutoff of Section 4
+ * (Section 5.2, Table 2 for its measured slopes): the smallest r with every
+ * normalised block
  * of the pairwise correction below `tol` for all larger separations
  * (VF relative to 1/(6 pi eta a); with torques != 0 also WT relative to
  * 1/(8 pi eta a^3) and WF relative to their geometric mean). Host only. */
@@ -398,7 +422,8 @@ int fcm_server_destroy(fcm_server* s);
 int fcm_pair_correction_noalloc(const fcm_params* p, int n, const void* pos, const void* F, const void* T,
                                 void* U, void* W, void* stream);
 
-/* Message of the last failed call on this thread ("" if none). */
+/* Message of the last failed call on this thread ("" if none). (Error
+ * reporting: no counterpart in the paper.) */
 const char* fcm_last_error(void);
 
 #ifdef __cplusplus
