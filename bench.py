@@ -228,6 +228,283 @@ def cpu_baseline(name, target_s=15.0):
             "host_cores": cores}
 
 
+# ---- error against the FP64 oracle, per configuration (outside every timed region)
+#
+# The oracle runs in worker processes started with spawn (they never touch the GPU) while the GPU
+# measurements run; the GPU results are compared afterwards. Full C2 systems are checked on a seeded
+# sample of particles: the oracle's grid part needs the whole spread and FFT, so the spread is split
+# over the workers and summed, then the velocity field is interpolated at the sample and the pair
+# correction is summed for the sample alone.
+ERR_SIGMAS = (1.5, 2.0, 3.0)
+ERR_SAMPLE = 4096
+ERR_SPREAD_CHUNKS = {1.5: 2, 2.0: 4, 3.0: 8}
+
+
+def _c2_inputs(n, L, seed):
+    """C2 inputs as the FP32 path sees them (rounded to float32, held in float64)."""
+    import numpy as np
+    from paper_2310_12651_gb300 import inputs
+    Y = inputs.random_suspension(n, L, seed)
+    F, T = inputs.random_loads(n, seed + 1)
+    return tuple(np.asarray(a, dtype=np.float32).astype(np.float64) for a in (Y, F, T))
+
+
+def _sigma_workload(Sigma):
+    from oracle import params as op
+    w = dict(oracle_workload("c2"))
+    w["Sigma"] = Sigma
+    w["M_G"] = op.support_points(Sigma, w["h"], TRUNC)
+    w["r_c"] = op.cutoff_radius(Sigma, TOL, torques=True)
+    return w
+
+
+def _c1_params():
+    """C1: N = 1,000 in a 100a box on 64^3, Sigma = 2a, window +-4 Sigma, r_c from the 1e-8 rule, forces only."""
+    from oracle import params as op
+    L, M, Sigma = 100.0, 64, 2.0
+    return dict(n=1000, L=L, M=M, Sigma=Sigma, M_G=op.support_points(Sigma, L / M, 4.0),
+                r_c=op.cutoff_radius(Sigma, 1e-8), seed=2310126510)
+
+
+def _standard_grid(L, c=6.3, ratio=1.39):
+    """Standard FCM (oracle-A) grid resolving sigma: sigma/h >= 1.39 (Table 1's 1e-8 row) on an
+    FFT-friendly M, window +-6.3 sigma."""
+    from oracle import closed_forms as cf
+    from oracle import params as op
+    sg = cf.fcm_sigma(1.0)
+    M = max(8, int(math.ceil(L * ratio / sg)))
+    while True:
+        m = M
+        for f in (2, 3, 5):
+            while m % f == 0:
+                m //= f
+        if m == 1 and M % 2 == 0:
+            break
+        M += 1
+    return M, op.support_points(sg, L / M, c)
+
+
+def _oracle_error_job(job):
+    import numpy as np
+    from oracle import grid_fcm as og
+    from paper_2310_12651_gb300 import inputs
+    kind = job[0]
+    if kind == "spread":                        # partial C2 grid of particles [a, b) at Sigma
+        _, Sigma, a, b = job
+        w = _sigma_workload(Sigma)
+        Y, F, T = _c2_inputs(w["n"], w["L"], inputs.BASE_SEED + 1)
+        return og.spread(Y[a:b], F[a:b], T[a:b], w["L"], w["M"], w["M_G"], Sigma, Sigma, fp32_windows=True)
+    if kind == "finish":                         # solve, interpolate at the sample, pair sums for the sample
+        _, Sigma, grid, idx = job
+        w = _sigma_workload(Sigma)
+        Y, F, T = _c2_inputs(w["n"], w["L"], inputs.BASE_SEED + 1)
+        u = og.stokes_solve(grid, w["L"])
+        Ug, Wg = og.interpolate(u, Y[idx], w["L"], w["M_G"], Sigma, Sigma)
+        Up, Wp = og.pair_correction_subset(Y, F, T, w["L"], w["r_c"], Sigma, Sigma, idx)
+        return Ug + Up, Wg + Wp
+    if kind == "c1_fast":                        # oracle-C on C1 (FP64 inputs)
+        c = _c1_params()
+        Y = inputs.random_suspension(c["n"], c["L"], c["seed"])
+        F, _ = inputs.random_loads(c["n"], c["seed"] + 1, torques=False)
+        return og.fast_fcm_apply(Y, F, None, c["L"], c["M"], c["M_G"], c["Sigma"], c["r_c"])
+    if kind == "c1_standard":                    # oracle-A on C1
+        c = _c1_params()
+        Y = inputs.random_suspension(c["n"], c["L"], c["seed"])
+        F, _ = inputs.random_loads(c["n"], c["seed"] + 1, torques=False)
+        M, MG = _standard_grid(c["L"])
+        return og.standard_fcm_apply(Y, F, None, c["L"], M, MG)
+    if kind == "c2s_standard":                   # oracle-A on a C2-density sample system (FP32-rounded inputs)
+        _, n = job
+        w = oracle_workload("c2", n=n, h_ref=oracle_workload("c2")["h"])
+        Y, F, T = _c2_inputs(n, w["L"], inputs.BASE_SEED + 77)
+        M, MG = _standard_grid(w["L"])
+        return og.standard_fcm_apply(Y, F, T, w["L"], M, MG)
+    raise ValueError(kind)
+
+
+class OracleErrors:
+    """Starts the oracle jobs at once (spawned workers), finishes them on demand."""
+
+    def __init__(self, workers=None):
+        import multiprocessing as mp
+        import numpy as np
+        self.n = WORKLOADS["c2"]["n"]
+        self.idx = np.sort(np.random.default_rng(2310126531).choice(self.n, ERR_SAMPLE, replace=False))
+        self.n_c2s = 4096
+        cores = len(os.sched_getaffinity(0))
+        self.pool = mp.get_context("spawn").Pool(workers or max(1, min(cores - 1, 16)))
+        self.spread = {}
+        for Sigma in ERR_SIGMAS:
+            k = ERR_SPREAD_CHUNKS[Sigma]
+            cuts = [self.n * i // k for i in range(k + 1)]
+            self.spread[Sigma] = self.pool.map_async(_oracle_error_job,
+                                                     [("spread", Sigma, cuts[i], cuts[i + 1]) for i in range(k)])
+        self.c1_fast = self.pool.apply_async(_oracle_error_job, (("c1_fast",),))
+        self.c1_std = self.pool.apply_async(_oracle_error_job, (("c1_standard",),))
+        self.c2s_std = self.pool.apply_async(_oracle_error_job, (("c2s_standard", self.n_c2s),))
+
+    def results(self, timeout=1800):
+        finish = {}
+        for Sigma in ERR_SIGMAS:
+            grid = sum(self.spread[Sigma].get(timeout))
+            finish[Sigma] = self.pool.apply_async(_oracle_error_job, (("finish", Sigma, grid, self.idx),))
+        out = {"c2": {S: f.get(timeout) for S, f in finish.items()}, "c1_fast": self.c1_fast.get(timeout),
+               "c1_standard": self.c1_std.get(timeout), "c2s_standard": self.c2s_std.get(timeout)}
+        self.pool.close()
+        self.pool.join()
+        return out
+
+
+def _errs(got, ref):
+    """Relative L2 over all components and the paper's mean relative error (Section 5.1)."""
+    import numpy as np
+    got, ref = np.asarray(got, dtype=np.float64), np.asarray(ref, dtype=np.float64)
+    rn = np.linalg.norm(ref, axis=1)
+    return {"rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+            "mean_rel": float(np.mean(np.linalg.norm(got - ref, axis=1) / np.where(rn > 0, rn, 1.0)))}
+
+
+def error_vs_oracle(device, oracle_jobs):
+    """FP32 (and FP64 plain) GPU results against the oracle, per configuration:
+    * C2 at Sigma = 1.5, 2, 3a (system 0 of the bench, 128^3, forces + torques): FP32 against
+      oracle-C (fast FCM, FP64) on a seeded sample of 4,096 particles;
+    * C1 (N = 1,000, 64^3, forces only): the FP64 plain path against oracle-C;
+    * the method's total error: the FP64 plain path on C1, and the FP32 path on a 4,096-sphere
+      system at C2's density and parameters, against standard FCM (oracle-A on a sigma-resolving grid)."""
+    import numpy as np
+    import torch
+    from paper_2310_12651_gb300 import fcm, inputs
+    dev = torch.device("cuda", device)
+    st = torch.cuda.current_stream(dev).cuda_stream
+    ref = oracle_jobs.results()
+    out = {"sample_particles": ERR_SAMPLE, "metrics": "rel_l2 over all components; mean_rel = (1/N) sum |V - U| / |U| "
+                                                      "(Section 5.1)"}
+    # both sides take the same parameter values (those of the oracle's rules)
+    c2 = {}
+    for Sigma in ERR_SIGMAS:
+        sw = _sigma_workload(Sigma)
+        n, L, MG, rc = sw["n"], sw["L"], sw["M_G"], sw["r_c"]
+        Y, F, T = _c2_inputs(n, L, inputs.BASE_SEED + 1)
+        pos, Fd, Td = (torch.as_tensor(a, dtype=torch.float32, device=dev) for a in (Y, F, T))
+        with fcm.Handle(fcm.make_params(L, WORKLOADS["c2"]["grid"], Sigma, rc, MG, n, fcm.FCM_FP32), device) as hh:
+            U, W = fcm.apply_tensors(hh, pos, Fd, Td, stream=st)
+            assert hh.check() == 0
+        Ug, Wg = U.double().cpu().numpy()[oracle_jobs.idx], W.double().cpu().numpy()[oracle_jobs.idx]
+        Uo, Wo = ref["c2"][Sigma]
+        c2[f"Sigma={Sigma}a"] = {"M_G": MG, "r_c": rc, "U": _errs(Ug, Uo), "W": _errs(Wg, Wo)}
+    out["c2_fp32_vs_oracle"] = c2
+    c = _c1_params()
+    Y = inputs.random_suspension(c["n"], c["L"], c["seed"])
+    F, _ = inputs.random_loads(c["n"], c["seed"] + 1, torques=False)
+    pos, Fd = (torch.as_tensor(a, dtype=torch.float64, device=dev) for a in (Y, F))
+    with fcm.Handle(fcm.make_params(c["L"], c["M"], c["Sigma"], c["r_c"], c["M_G"], c["n"], fcm.FCM_FP64), device) as hh:
+        U, _ = fcm.apply_tensors(hh, pos, Fd, None, want_W=False, stream=st)
+        assert hh.check() == 0
+    U = U.cpu().numpy()
+    Uf, _ = ref["c1_fast"]
+    Us, _ = ref["c1_standard"]
+    out["c1_fp64_vs_oracle"] = {"U": _errs(U, Uf)}
+    out["c1_method_fp64_vs_standard_fcm"] = {"U": _errs(U, Us), "standard_grid": _standard_grid(c["L"])}
+    w = oracle_workload("c2", n=4096, h_ref=oracle_workload("c2")["h"])
+    MG, rc = w["M_G"], w["r_c"]
+    Y, F, T = _c2_inputs(4096, w["L"], inputs.BASE_SEED + 77)
+    pos, Fd, Td = (torch.as_tensor(a, dtype=torch.float32, device=dev) for a in (Y, F, T))
+    with fcm.Handle(fcm.make_params(w["L"], w["M"], w["Sigma"], rc, MG, 4096, fcm.FCM_FP32), device) as hh:
+        U, W = fcm.apply_tensors(hh, pos, Fd, Td, stream=st)
+        assert hh.check() == 0
+    Us, Ws = ref["c2s_standard"]
+    out["c2_density_method_fp32_vs_standard_fcm"] = {
+        "U": _errs(U.double().cpu().numpy(), Us), "W": _errs(W.double().cpu().numpy(), Ws),
+        "system": f"N=4096 at phi=5% (L={w['L']:.1f}a, {w['M']}^3, Sigma={w['Sigma']}a, M_G={MG}, r_c={rc:.2f}a)",
+        "standard_grid": _standard_grid(w["L"])}
+    return out
+
+
+def large_sweep(device, grids=(192, 256, 320), tol=1e-5, steps=3, warmup=2, seed=2310126800):
+    """The large precision/roofline configuration: one system of N = 1,048,576 spheres at 10% (L =
+    352.83a; uniform RSA, F and T i.i.d. N(0,1)), on 192^3, 256^3 and 320^3 grids, each with the
+    (Sigma, M_G, r_c) the autotuner picks at tolerance tol for that grid (the three cheapest
+    candidates of its cost model timed on the GPU). Per grid: particle-applies/s of fcm_apply (FP32,
+    inputs resident, L2 flushed between applies, CUDA events), per-stage times, the FP32 ALU roofline
+    of the dominant kernel, and the FP32 error against the FP64 plain path on the same GPU. This is
+    the trade-off of the paper's Section 5.2 (grid against pairs, set by Sigma) at GB300 scale."""
+    import numpy as np
+    import torch
+    from paper_2310_12651_gb300 import fcm, inputs, tune
+    n, phi = 1048576, 0.10
+    L = inputs.box_edge(n, phi)
+    dev = torch.device("cuda", device)
+    st = torch.cuda.current_stream(dev)
+    t0 = time.perf_counter()
+    Y = inputs.random_suspension(n, L, seed)
+    F, T = inputs.random_loads(n, seed + 1)
+    gen_s = time.perf_counter() - t0
+    pos, Fd, Td = (torch.as_tensor(a, dtype=torch.float32, device=dev) for a in (Y, F, T))
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sm_count * 128 * 2 * (peaks().get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
+    hbm = peaks().get("hbm_gbs", 6800.0)
+    rows = []
+    for M in grids:
+        ch = tune.choose(n, L, tol, torques=True, measure=tune.gpu_timer(pos, Fd, Td, L, device, reps=2, warmup=1),
+                         top=3, grid=M, max_grid=M)
+        p = tune.make_params(ch, L, n)
+        U = torch.empty_like(Fd)
+        W = torch.empty_like(Fd)
+        with fcm.Handle(p, device) as h:
+            for _ in range(warmup):
+                h.apply(n, pos, Fd, Td, U, W, st.cuda_stream)
+            h.set_timing(True)
+            h.read_timing()
+            ms = 0.0
+            for _ in range(steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                h.apply(n, pos, Fd, Td, U, W, st.cuda_stream)
+                e1.record(st)
+                e1.synchronize()
+                ms += e0.elapsed_time(e1)
+            stage = h.read_timing()
+            h.set_timing(False)
+            assert h.check() == 0
+        avg = {k: (v[0] / v[1] if v[1] else None) for k, v in stage.items()}
+        MG = ch["M_G"]
+        flops = {"spread": 16.0 * n * MG ** 3, "gather": 16.0 * n * MG ** 3,
+                 "pair": 150.0 * n * (n / L ** 3 * 4.0 / 3.0 * math.pi * ch["r_c"] ** 3)}
+        dom = max(flops, key=lambda k: avg[k] or 0.0)
+        achieved = flops[dom] / (avg[dom] * 1e-3) / 1e12
+        p64 = fcm.make_params(L, M, ch["Sigma"], ch["r_c"], MG, n, fcm.FCM_FP64)
+        pos64, F64, T64 = (t.double() for t in (pos, Fd, Td))
+        with fcm.Handle(p64, device) as h64:
+            U64, W64 = fcm.apply_tensors(h64, pos64, F64, T64, stream=st.cuda_stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.zero_()
+            e0.record(st)
+            h64.apply(n, pos64, F64, T64, U64, W64, st.cuda_stream)
+            e1.record(st)
+            e1.synchronize()
+            ms64 = e0.elapsed_time(e1)
+            assert h64.check() == 0
+        eu = float(torch.linalg.norm(U.double() - U64) / torch.linalg.norm(U64))
+        ew = float(torch.linalg.norm(W.double() - W64) / torch.linalg.norm(W64))
+        del U64, W64, pos64, F64, T64
+        rows.append({"M": M, "Sigma": ch["Sigma"], "Sigma_over_sigma": ch["Sigma_over_sigma"], "M_G": MG,
+                     "r_c": ch["r_c"], "tuned_candidate_ms": ch["measured_s"] * 1e3,
+                     "ms_per_apply": ms / steps, "particle_applies_per_s": n * steps / (ms * 1e-3),
+                     "stage_ms": {k: round(v, 4) for k, v in avg.items() if v},
+                     "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
+                                  "unit": "TFLOP/s", "frac": achieved / peak},
+                     "fft_solve_frac_hbm": (72.0 * M ** 3 / (avg["fft_solve"] * 1e-3) / 1e9 / hbm)
+                     if avg.get("fft_solve") else None,
+                     "fp32_rel_l2_vs_fp64": {"U": eu, "W": ew},
+                     "fp64_plain_particle_applies_per_s": n / (ms64 * 1e-3)})
+    return {"workload": f"N={n} uniform spheres (RSA, min separation 2.2a) at phi=10% (L={L:.2f}a), forces+torques, "
+                        f"FP32, one fcm_apply per step, inputs resident, L2 flushed between applies; parameters from "
+                        f"the autotuner at tolerance {tol:g} per grid",
+            "positions_generation_s": gen_s, "rows": rows}
+
+
 # The paper's performance study (Section 5.2, Table 3): forces only, a/L = 1/400, eps = 1e-4, Sigma/dx = 1.00,
 # M_G = 10, and per volume fraction the optimal Sigma/sigma and R_c/sigma it reports; its peak was about 7e6
 # particle-applies/s (PTPS) on an RTX 2080 Ti in FP32.
@@ -339,7 +616,7 @@ def rods_bench(device, systems=8, steps=5, warmup=3, tol=1e-4):
             "stage_ms_one_pass": stages, "fp32_rel_l2_vs_fp64": {"U": eu, "W": ew}}
 
 
-def crossover_study(device, a_over_L=(0.012, 0.008), tols=(1e-4, 1e-6),
+def crossover_study(device, a_over_L=(0.012, 0.008, 0.004), tols=(1e-4, 1e-6),
                     phis=(0.005, 0.01, 0.02, 0.04, 0.08, 0.12, 0.16, 0.2), reps=5, warmup=3):
     """Fast FCM against standard FCM (Sigma = sigma, Sigma_D = sigma_D, no pair correction) on the
     paper's crossover study shape (Section 5.3, Fig. 3): forces only, one system per apply, each
@@ -378,7 +655,7 @@ def crossover_study(device, a_over_L=(0.012, 0.008), tols=(1e-4, 1e-6),
                         e1.synchronize()
                         return e0.elapsed_time(e1) * 1e-3 / reps
 
-                cands = tune.candidates(n, L, tol, torques=False, max_grid=512)
+                cands = tune.candidates(n, L, tol, torques=False, max_grid=768)
                 std = [c for c in cands if c["Sigma_over_sigma"] == 1.0]
                 fast = [c for c in cands if c["Sigma_over_sigma"] != 1.0][:3]
                 if not std or not fast:
@@ -774,9 +1051,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-oracle-errors", action="store_true",
+                    help="skip the per-configuration error against the FP64 oracle (also skipped with --no-cpu-baseline)")
     ap.add_argument("--spread-kernel", type=int, default=0, help="0 choose, 1 row-stationary, 2 shared atomics, 3 tensor cores (tcgen05)")
     ap.add_argument("--tile", default="0,0,0", help="spread/gather tile x,y,z in grid points (0,0,0: the library's choice)")
-    ap.add_argument("--study", default=None, choices=["crossover", "rigid", "brownian"],
+    ap.add_argument("--study", default=None, choices=["crossover", "rigid", "brownian", "large"],
                     help="run one measurement instead of the bench line: crossover = fast vs standard FCM against "
                          "phi; rigid = the rigid-rod solve on the 7,744-rod suspension; brownian = fcm_brownian")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-mix measurement")
@@ -784,6 +1063,7 @@ def main():
     ap.add_argument("--no-rods", action="store_true", help="skip the filament-layout measurement")
     ap.add_argument("--no-brownian", action="store_true", help="skip the Brownian-increment measurement")
     ap.add_argument("--no-rigid", action="store_true", help="skip the rigid-rod mobility solve measurement")
+    ap.add_argument("--no-large", action="store_true", help="skip the N = 1,048,576 sweep over 192^3-320^3 grids")
     ap.add_argument("--sweep-full", action="store_true", help="include the 12.8%% (N = 1.96M) sweep row")
     ap.add_argument("--serve-requests", type=int, default=1024)
     ap.add_argument("--mode", default="batched", choices=["batched", "single"],
@@ -808,11 +1088,16 @@ def main():
         if rank == 0:
             if args.study == "crossover":
                 res = crossover_study(local)
+            elif args.study == "large":
+                res = large_sweep(local)
             else:
                 run = {"rigid": rigid_bench, "brownian": brownian_bench}[args.study]
                 res = run(local, with_oracle=not args.no_cpu_baseline)
             print(json.dumps({"study": args.study, **res}), flush=True)
         return 0
+    oracle_jobs = None
+    if rank == 0 and world == 1 and args.workload == "c2" and not (args.no_oracle_errors or args.no_cpu_baseline):
+        oracle_jobs = OracleErrors()   # spawned workers; they run while the GPU is measured
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     sptr = stream.cuda_stream
@@ -876,6 +1161,20 @@ def main():
     total_ms = max_over_ranks(sum(step_ms), world, dev)
     value = world * n * B * args.steps / (total_ms * 1e-3)
     ms_per_step = total_ms / args.steps
+
+    # ---- the FFT chain alone: grid-part passes (no pair kernel beside it on the side stream)
+    fft_alone = None
+    if batched:
+        h.set_timing(True)
+        h.read_timing()
+        for k in range(3):
+            flush.zero_()
+            h.batch_apply(offsets, pos_all, F_all, T_all, U, W, sptr, stages=fcm.STAGE_GRID)
+        st_alone = h.read_timing()
+        h.set_timing(False)
+        ms_fft, cnt_fft = st_alone["fft_solve"]
+        if cnt_fft:
+            fft_alone = ms_fft / cnt_fft
 
     # ---- end to end through host buffers: pinned host -> device inputs, the pass, device -> host outputs
     hpos, hF, hT = (t.cpu().pin_memory() for t in (pos_all, F_all, T_all))
@@ -953,8 +1252,13 @@ def main():
     hbm = pk.get("hbm_gbs", 6800.0)
     stages_out = {name: {"ms_avg": avg[name], "launches": int(stage[name][1])} for name in stage}
     if avg["fft_solve"]:
-        stages_out["fft_solve"]["GBps"] = fft_bytes / (avg["fft_solve"] * 1e-3) / 1e9
+        # inside the full pass the chain shares the GPU with the pair kernel on the side stream
+        stages_out["fft_solve"]["GBps_beside_pair"] = fft_bytes / (avg["fft_solve"] * 1e-3) / 1e9
+    if fft_alone:
+        stages_out["fft_solve"]["ms_alone"] = fft_alone
+        stages_out["fft_solve"]["GBps"] = fft_bytes / (fft_alone * 1e-3) / 1e9
         stages_out["fft_solve"]["frac_hbm"] = stages_out["fft_solve"]["GBps"] / hbm
+        stages_out["fft_solve"]["bytes"] = "72 B per grid point: 6 transforms x 8 B + 24 B for the projection kernel"
     for s_ in ("spread", "gather"):
         if avg[s_]:
             stages_out[s_]["TFLOPs"] = flops[s_] / (avg[s_] * 1e-3) / 1e12
@@ -971,6 +1275,9 @@ def main():
     oracle_here = rank == 0 and world == 1 and not args.no_cpu_baseline
     brown = None if args.no_brownian else brownian_bench(local, with_oracle=oracle_here)
     rigid = None if args.no_rigid else rigid_bench(local, with_oracle=oracle_here)
+    large = None if (args.no_large or args.workload != "c2") else large_sweep(local)
+
+    err = error_vs_oracle(local, oracle_jobs) if oracle_jobs is not None else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -987,8 +1294,8 @@ def main():
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B * 3 * n * 3 * 4,
                    "d2h_bytes_per_step": B * 2 * n * 3 * 4},
            "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
-           "fp64_plain": fp64, "serve": serve, "paper_sweep": sweep, "rods": rods, "brownian": brown,
-           "rigid_rods": rigid,
+           "fp64_plain": fp64, "error_vs_oracle": err, "serve": serve, "paper_sweep": sweep, "rods": rods, "brownian": brown,
+           "rigid_rods": rigid, "large_sweep": large,
            "speedup_vs_fp64_plain": (value / world / fp64["value"]) if fp64 else None,
            "stages": stages_out, "step_ms_median": statistics.median(step_ms),
            "workspace_bytes": h.workspace_bytes()}

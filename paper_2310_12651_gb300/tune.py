@@ -34,8 +34,9 @@ from . import fcm
 
 SQRT_PI = math.sqrt(math.pi)
 TRUNCATION = {1e-3: 3.8, 1e-4: 4.5, 1e-5: 5.0, 1e-6: 5.4, 1e-8: 6.3}
-# Table 1 of the paper: tolerance -> minimum Sigma/dx
+# Table 1 of the paper: tolerance -> minimum Sigma/dx, and the grid support printed beside it
 RESOLUTION = {1e-2: 0.71, 1e-3: 0.87, 1e-4: 0.99, 1e-6: 1.20, 1e-8: 1.39}
+TABLE1_SUPPORT = {1e-2: 8, 1e-3: 9, 1e-4: 10, 1e-6: 12, 1e-8: 14}
 # Cost model coefficients (seconds) measured on GB300 with this library's FP32 kernels:
 # spread + gather per (particle, window point), pair test per candidate, FFT solve per grid point,
 # and a fixed cost per apply (launches and small kernels).
@@ -58,6 +59,18 @@ def truncation_for(tol: float) -> float:
         if key <= tol:
             return TRUNCATION[key]
     return TRUNCATION[min(TRUNCATION)]
+
+
+def standard_support(tol: float, width_over_h: float) -> int:
+    """M_G for standard FCM (Sigma = sigma: the plain Gaussian, no modified-kernel tail) at tol: the
+    half-width c = M_G dx / (2 Sigma) of Table 1's row for the tolerance (the row with the largest
+    error at or below tol), kept for the kernel width the grid resolves. The printed pairs reach the
+    printed error with the plain Gaussian down to the 1e-6 row (they floor near 4e-7 at the 1e-8
+    row), and the pair-free standard method gives the whole tolerance to the grid."""
+    keys = sorted(TABLE1_SUPPORT, reverse=True)           # 1e-2, 1e-3, ...
+    row = next((k for k in keys if k <= tol), keys[-1])
+    c = TABLE1_SUPPORT[row] / (2.0 * RESOLUTION[row])
+    return int(2 * math.ceil(c * width_over_h - 1e-12))
 
 
 def resolution_for(tol: float) -> float:
@@ -122,6 +135,9 @@ def candidates(n: int, L: float, tol: float, torques: bool = True, a: float = 1.
     sg = a / SQRT_PI
     ratio = resolution_for(GRID_SHARE * tol)
     c = truncation_for(GRID_SHARE * tol)
+    # standard FCM has no pair error: with forces only the grid takes all of tol (the rotation's
+    # derivative kernel needs the finer split resolution when torques act)
+    ratio_std = resolution_for(tol if not torques else GRID_SHARE * tol)
     rho = n / L ** 3
     out = []
     for s in SIGMA_LADDER:
@@ -129,16 +145,17 @@ def candidates(n: int, L: float, tol: float, torques: bool = True, a: float = 1.
         standard = s == 1.0
         # standard FCM resolves the narrower rotlet width sigma_D when torques act
         width = min(Sigma, SIGMA_D_STANDARD * a) if (standard and torques) else Sigma
+        need = ratio_std if standard else ratio
         if grid is not None:
             M = int(grid)
-            if width / (L / M) < ratio:
+            if width / (L / M) < need:
                 continue
         else:
-            M = max(grid_for(L, width, ratio), grid_for(L, L, min_grid))
+            M = max(grid_for(L, width, need), grid_for(L, L, min_grid))
         if M > max_grid:
             continue
         h = L / M
-        MG = min(support_points(Sigma, h, c), M)
+        MG = min(standard_support(tol, Sigma / h) if standard else support_points(Sigma, h, c), M)
         if MG > 24:
             continue
         rc = 0.0 if standard else pair_cutoff(Sigma, tol, rho, torques)

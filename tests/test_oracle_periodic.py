@@ -286,10 +286,16 @@ def test_cutoff_rule_against_table2():
 
 @pytest.mark.slow
 def test_grid_error_against_table1():
-    """The grid part at the first three Table 1 settings reaches the printed error within a factor 2.
+    """Table 1 (Section 5.1) against the direct Fourier sum, with every pair corrected (R_c = L/2).
 
-    The error is the paper's mean relative particle error against a converged
-    reference (here the direct Fourier sum), with every pair corrected.
+    The error is the paper's mean relative particle error. Two readings are pinned:
+    * the printed (Sigma/dx, M_G) pairs, M_G consecutive points per direction: the first three rows
+      reach the printed error within a factor 2; the 1e-6 and 1e-8 rows cannot, because every printed
+      pair truncates the kernel near +-5 Sigma (c = M_G dx / (2 Sigma) = 5.0 ... 5.6), where the
+      modified kernel's tail floors the error near 1e-5;
+    * the printed Sigma/dx with a window wide enough not to truncate (+-7 Sigma): all five rows
+      reach the printed error within a factor 2, so the Sigma/dx column is the resolution the
+      tolerance needs, and the M_G column is not a truncation that reaches 1e-6 or 1e-8.
     """
     rows = _golden("table1_grid_resolution.txt")
     n = 200
@@ -299,12 +305,21 @@ def test_grid_error_against_table1():
     Ub, _ = ss.apply(Y, F, None, L)
     Sigma = 1.1
     rc = min(pr.cutoff_radius(Sigma, 1e-12), 0.5 * L)
-    for eps, ratio, MG in rows[:3]:
+
+    def err_at(M, MG):
+        U, _ = g.fast_fcm_apply(Y, F, None, L, M, MG, Sigma, rc)
+        return np.mean(np.linalg.norm(U - Ub, axis=1) / np.linalg.norm(Ub, axis=1))
+
+    for k, (eps, ratio, MG) in enumerate(rows):
         eps, ratio, MG = float(eps), float(ratio), int(MG)
         M = int(round(L / (Sigma / ratio)))
-        U, _ = g.fast_fcm_apply(Y, F, None, L, M, MG, Sigma, rc)
-        err = np.mean(np.linalg.norm(U - Ub, axis=1) / np.linalg.norm(Ub, axis=1))
-        assert eps / 2 <= err <= 2 * eps, (eps, err)
+        literal = err_at(M, MG)
+        if k < 3:
+            assert eps / 2 <= literal <= 2 * eps, (eps, literal)
+        else:
+            assert literal > 10 * eps, (eps, literal)   # the printed M_G truncates above the row's error
+        wide = err_at(M, min(M, 2 * int(math.ceil(7.0 * ratio))))
+        assert eps / 2 <= wide <= 2 * eps, (eps, wide)
 
 
 def test_pair_correction_subset_equals_full_rows():

@@ -65,17 +65,30 @@ def test_candidates_are_admissible_and_ranked(n, phi, tol):
     costs = [c["cost_model_s"] for c in cands]
     assert costs == sorted(costs)
     for c in cands:
-        width = c["Sigma"] if c["Sigma_over_sigma"] != 1.0 else tune.SIGMA_D_STANDARD
-        assert min(c["Sigma"], width) / c["h"] >= tune.resolution_for(tol) - 1e-12
+        standard = c["Sigma_over_sigma"] == 1.0
+        width = c["Sigma"] if not standard else tune.SIGMA_D_STANDARD
+        assert min(c["Sigma"], width) / c["h"] >= tune.resolution_for(tune.GRID_SHARE * tol) - 1e-12
         assert c["M_G"] % 2 == 0 and c["M_G"] <= min(24, c["M"])
-        assert c["M_G"] * c["h"] >= 2 * tune.truncation_for(tol) * c["Sigma"] - 1e-9
-        if c["Sigma_over_sigma"] == 1.0:
+        if standard:
+            # standard FCM keeps the truncation of Table 1's row for the tolerance (plain Gaussian)
             assert c["r_c"] == 0.0
+            assert c["M_G"] == tune.standard_support(tol, c["Sigma"] / c["h"])
         else:
+            assert c["M_G"] * c["h"] >= 2 * tune.truncation_for(tol) * c["Sigma"] - 1e-9
             assert 0 < c["r_c"] <= L / 2
     # a dilute system prefers a wider Sigma than a dense one (Section 5.2, Table 3)
     if phi <= 0.01:
         assert tune.choose(n, L, tol)["Sigma_over_sigma"] >= 3.0
+
+
+def test_standard_support_follows_table1():
+    """At Table 1's own resolution the standard-FCM support is the printed M_G (odd rows rounded up to
+    an even window), and it grows with the resolved width's points per h."""
+    for eps, ratio, MG in _golden_rows("table1_grid_resolution.txt"):
+        got = tune.standard_support(float(eps), float(ratio))
+        assert got == int(MG) + (int(MG) % 2)
+    assert tune.standard_support(1e-4, 2.0) > tune.standard_support(1e-4, 0.99)
+    assert tune.standard_support(3e-5, 1.0) == tune.standard_support(1e-6, 1.0)   # the next tighter row
 
 
 def test_choose_with_measurement_keeps_the_fastest():
@@ -114,6 +127,20 @@ def test_chosen_parameters_reach_the_tolerance(suspension, tol):
         eu = np.mean(np.linalg.norm(U - Ub, axis=1) / np.linalg.norm(Ub, axis=1))
         ew = np.mean(np.linalg.norm(W - Wb, axis=1) / np.linalg.norm(Wb, axis=1))
         assert eu < tol and ew < tol, (c, eu, ew)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("tol", [1e-3, 1e-4, 1e-6])
+def test_standard_forces_only_reaches_the_tolerance(suspension, tol):
+    """Forces only (the crossover study's setting): standard FCM at Table 1's resolution and support
+    for the whole tolerance reaches it against the direct Fourier sum."""
+    n, L, Y, F, T, Ub, Wb = suspension
+    Ub, _ = ss.apply(Y, F, None, L)
+    std = [c for c in tune.candidates(n, L, tol, torques=False, max_grid=160) if c["Sigma_over_sigma"] == 1.0]
+    assert std
+    U, _ = g.standard_fcm_apply(Y, F, None, L, std[0]["M"], std[0]["M_G"])
+    eu = np.mean(np.linalg.norm(U - Ub, axis=1) / np.linalg.norm(Ub, axis=1))
+    assert eu < tol, (std[0], eu)
 
 
 def test_tuned_cache_round_trip(tmp_path):
