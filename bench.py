@@ -946,7 +946,7 @@ def serve_pool(seed=2310126900, pool=SERVE_POOL, tol=1e-4):
     return systems, classes
 
 
-def serve_bench(device, requests=1024, loads=(0.5, 0.9), seed=2310126950):
+def serve_bench(device, requests=1024, loads=(0.5, 0.9, 1.0, 2.0), seed=2310126950):
     """The serving engine on the mix: capacity with every request queued at once, then Poisson
     arrivals at fractions of that capacity; latency = submit to completion (host clocks)."""
     import threading

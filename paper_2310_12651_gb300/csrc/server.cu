@@ -9,6 +9,10 @@
 //     widths, cutoff, precision, torques or not) waiting at the same time are
 //     stacked into one fcm_batch_apply pass (continuous batching: whatever is
 //     queued when a launch slot frees up goes into the next pass);
+//   * a class has at most one pass in flight: requests that arrive while their
+//     class is on the GPU wait for that pass and join the class's next one (its
+//     passes would run one after the other anyway, since they share the cached
+//     handle's workspace), while other classes use the remaining slots;
 //   * batch handles (workspace, cell lists, cuFFT plans) stay resident in a
 //     cache keyed by grid class and capacity bucket, so a class's second pass
 //     plans and allocates nothing;
@@ -141,6 +145,7 @@ struct fcm_server {
   size_t hbm_bytes = 0;             // written by the worker, read under mu
   // worker-owned
   std::list<CachedHandle> cache;
+  std::unordered_map<std::string, int> class_in_flight;   // passes on the GPU per grid class (worker only)
   Slot slots[kSlots];
   size_t used = 0;                  // handles + staging device bytes
   unsigned long long tick = 0;
@@ -241,6 +246,10 @@ void complete_slot(fcm_server* s, Slot& sl, int status) {
   if (sl.ch) sl.ch->in_flight -= 1;
   sl.ch = nullptr;
   sl.busy = false;
+  if (!sl.reqs.empty()) {
+    auto it = s->class_in_flight.find(sl.reqs.front()->key);
+    if (it != s->class_in_flight.end() && it->second > 0) it->second -= 1;
+  }
   finish_requests(s, sl.reqs, status);
   sl.reqs.clear();
 }
@@ -354,11 +363,20 @@ int get_handle(fcm_server* s, const fcm_params& p, const std::string& key, bool 
 // batch limits. Called with s->mu held.
 std::vector<std::shared_ptr<Request>> take_batch(fcm_server* s) {
   std::vector<std::shared_ptr<Request>> b;
-  if (s->pending.empty()) return b;
-  const std::string key = s->pending.front()->key;
+  // the oldest request whose class has no pass in flight picks the class
+  const std::string* key = nullptr;
+  for (const auto& q : s->pending) {
+    auto it = s->class_in_flight.find(q->key);
+    if (it == s->class_in_flight.end() || it->second == 0) {
+      key = &q->key;
+      break;
+    }
+  }
+  if (!key) return b;
+  const std::string k = *key;
   long long total = 0;
   for (auto it = s->pending.begin(); it != s->pending.end() && (int)b.size() < s->max_batch;) {
-    if ((*it)->key == key && (b.empty() || total + (*it)->r.n <= (1LL << 28))) {
+    if ((*it)->key == k && (b.empty() || total + (*it)->r.n <= (1LL << 28))) {
       total += (*it)->r.n;
       (*it)->state = kRunning;
       b.push_back(*it);
@@ -514,8 +532,13 @@ void worker_main(fcm_server* s) {
       }
     }
     if (!batch.empty()) {
+      const std::string key = batch.front()->key;
       int rc = launch(s, *free_slot, batch);
-      if (rc != FCM_OK) finish_requests(s, batch, rc);
+      if (rc != FCM_OK) {
+        finish_requests(s, batch, rc);
+      } else {
+        s->class_in_flight[key] += 1;   // worker-owned, like the slots
+      }
     }
   }
   // shutdown: let passes in flight end (kernels are finite), then release everything
