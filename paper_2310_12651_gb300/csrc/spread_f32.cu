@@ -272,6 +272,11 @@ __global__ void __launch_bounds__(rows_threads(MGT), 1) spread_rows_kernel(Geome
 
 enum { kPencilForces = 0, kPencilSameWidth = 1, kPencilTwoWidths = 2 };
 
+// Particles staged per pass of the pencil kernel. Their raw rows (position, force, torque) are
+// fetched into a second buffer with asynchronous copies while the previous pass runs, so building
+// the profile tables reads shared memory only.
+constexpr int kPencilChunk = 128;
+
 // Register pairs of a pencil row: window pairs start at pair ox / 2 with ox in [0, 8).
 __host__ __device__ constexpr int pencil_pairs(int MGT) { return row_pairs(MGT) + 3; }
 
@@ -284,6 +289,7 @@ struct PencilTables {
   float4* pf;   // [chunk] F' = nrm F (two widths: F)
   float4* pt;   // [chunk] U' = tq T (two widths: T)
   int4* po;     // [chunk] (x offset in the tile, y and z window start in the region, tile step)
+  float4* raw;  // [2][3][chunk] raw rows: position, force, torque (double buffer)
   float* xk;    // two widths: [chunk][4 NK] d g_D along x, two pairs per float4
   float* xd;    // two widths: [chunk][2 NP] g_D along x
 };
@@ -291,22 +297,44 @@ struct PencilTables {
 template <int MGT>
 __device__ inline PencilTables pencil_tables(float4* sm) {
   constexpr int NP = row_pairs(MGT), NK = (NP + 1) / 2;
+  constexpr int C = kPencilChunk;
   PencilTables t;
   t.xa = sm;
-  t.xb = t.xa + kRowsChunk * NP;
-  t.yt = t.xb + kRowsChunk * NP;
-  t.zt = t.yt + kRowsChunk * MGT;
-  t.pf = t.zt + kRowsChunk * MGT;
-  t.pt = t.pf + kRowsChunk;
-  t.po = reinterpret_cast<int4*>(t.pt + kRowsChunk);
-  t.xk = reinterpret_cast<float*>(t.po + kRowsChunk);
-  t.xd = t.xk + kRowsChunk * 4 * NK;
+  t.xb = t.xa + C * NP;
+  t.yt = t.xb + C * NP;
+  t.zt = t.yt + C * MGT;
+  t.pf = t.zt + C * MGT;
+  t.pt = t.pf + C;
+  t.po = reinterpret_cast<int4*>(t.pt + C);
+  t.raw = reinterpret_cast<float4*>(t.po + C);
+  t.xk = reinterpret_cast<float*>(t.raw + 6 * C);
+  t.xd = t.xk + C * 4 * NK;
   return t;
 }
 
 __host__ __device__ constexpr size_t pencil_tables_bytes(int MGT) {
-  return sizeof(float4) * (size_t)kRowsChunk * (2 * row_pairs(MGT) + 2 * MGT + 3 + (row_pairs(MGT) + 1) / 2) +
-         sizeof(float) * (size_t)kRowsChunk * 2 * row_pairs(MGT);
+  return sizeof(float4) * (size_t)kPencilChunk * (2 * row_pairs(MGT) + 2 * MGT + 3 + 6 + (row_pairs(MGT) + 1) / 2) +
+         sizeof(float) * (size_t)kPencilChunk * 2 * row_pairs(MGT);
+}
+
+// Asynchronous 16-byte copy global -> shared (the raw rows of the next pass).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+
+// Raw rows of particles [base, base + np) into buffer `buf`.
+template <bool TORQUE>
+__device__ __forceinline__ void pencil_fetch(const PencilTables& tb, int buf, int base, int np,
+                                             const float4* __restrict__ pos, const float4* __restrict__ Fv,
+                                             const float4* __restrict__ Tv) {
+  float4* r = tb.raw + (size_t)buf * 3 * kPencilChunk;
+  for (int k = threadIdx.x; k < (TORQUE ? 3 : 2) * np; k += blockDim.x) {
+    const int a = k / np, q = k - a * np;
+    const float4* src = (a == 0 ? pos : (a == 1 ? Fv : Tv)) + base + q;
+    cp_async16(r + a * kPencilChunk + q, src);
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
 __device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
@@ -429,16 +457,24 @@ __global__ void __launch_bounds__(rows_threads(MGT), 1) spread_pencil_kernel(Geo
   const PencilTables tb = pencil_tables<MGT>(sm4);
   int cur = 0;   // tile step whose x origin anchors the register row
 
-  for (int base = p_begin; base < p_end; base += kRowsChunk) {
-    const int np = min(kRowsChunk, p_end - base);
-    __syncthreads();
+  pencil_fetch<TORQUE>(tb, 0, p_begin, min(kPencilChunk, p_end - p_begin), pos, Fv, Tv);
+  int buf = 0;
+  for (int base = p_begin; base < p_end; base += kPencilChunk, buf ^= 1) {
+    const int np = min(kPencilChunk, p_end - base);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();   // this pass's raw rows are in; every warp is done with the previous tables
+    if (base + np < p_end)
+      pencil_fetch<TORQUE>(tb, buf ^ 1, base + np, min(kPencilChunk, p_end - base - np), pos, Fv, Tv);
+    const float4* rpos = tb.raw + (size_t)buf * 3 * kPencilChunk;
+    const float4* rF = rpos + kPencilChunk;
+    const float4* rT = rF + kPencilChunk;
     // y and z profiles {g, d, A + B d^2 (y) or B d^2 (z), g_D}
     for (int k = threadIdx.x; k < np * 2 * MGT; k += blockDim.x) {
       const int q = k / (2 * MGT);
       const int rem = k - q * 2 * MGT;
       const int d = 1 + rem / MGT;
       const int j = rem - (d - 1) * MGT;
-      const float4 y = pos[base + q];
+      const float4 y = rpos[q];
       const float yd = d == 1 ? y.y : y.z;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
       if (j < MG) {
@@ -454,7 +490,7 @@ __global__ void __launch_bounds__(rows_threads(MGT), 1) spread_pencil_kernel(Geo
     for (int k = threadIdx.x; k < np * 2 * NP; k += blockDim.x) {
       const int q = k / (2 * NP);
       const int slot = k - q * 2 * NP;
-      const float4 y = pos[base + q];
+      const float4 y = rpos[q];
       const int i0 = window_start_d(g, 0, y.x);
       const int j = slot - (wrap_once(i0, g.M[0]) & 1);
       float gs = 0.f, q2 = 0.f, dg = 0.f, gd = 0.f;
@@ -468,7 +504,7 @@ __global__ void __launch_bounds__(rows_threads(MGT), 1) spread_pencil_kernel(Geo
       float* ea = reinterpret_cast<float*>(tb.xa + (size_t)q * NP + (slot >> 1)) + (slot & 1);
       ea[0] = gs;
       if (MODE == kPencilSameWidth) {
-        const float4 f = Fv[base + q], t = Tv[base + q];
+        const float4 f = rF[q], t = rT[q];
         const float bn = kc.B * kc.nrm;
         float* eb = reinterpret_cast<float*>(tb.xb + (size_t)q * NP + (slot >> 1)) + (slot & 1);
         ea[2] = bn * f.x * q2;
@@ -483,7 +519,7 @@ __global__ void __launch_bounds__(rows_threads(MGT), 1) spread_pencil_kernel(Geo
       }
     }
     for (int q = threadIdx.x; q < np; q += blockDim.x) {
-      const float4 y = pos[base + q];
+      const float4 y = rpos[q];
       const int3 i0 = window_starts(g, y);
       const int wx = wrap_once(i0.x, g.M[0]);
       const int step = min(max(wx >> 3, 0), ntx - 1);
@@ -493,8 +529,8 @@ __global__ void __launch_bounds__(rows_threads(MGT), 1) spread_pencil_kernel(Geo
       off.z = min(max(wrap_once(i0.z, g.M[2]) - oz0, 0), g.tile[2] - 1);
       off.w = step;
       tb.po[q] = off;
-      const float4 f = Fv[base + q];
-      const float4 t = TORQUE ? Tv[base + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 f = rF[q];
+      const float4 t = TORQUE ? rT[q] : make_float4(0.f, 0.f, 0.f, 0.f);
       if (MODE == kPencilTwoWidths) {
         tb.pf[q] = f;
         tb.pt[q] = t;
