@@ -51,7 +51,12 @@ WORKLOADS = {
 }
 # dram__bytes_read.sum + dram__bytes_write.sum per system of a launch (cold caches), from one ncu capture of
 # the current kernels; a launch over B systems moves B times this. None once a kernel changes after the capture.
-TRAFFIC_BYTES = {"c2": {"spread": 28.90e6, "gather": 26.61e6, "pair": 3.18e6}}
+TRAFFIC_BYTES = {"c2": {"spread": 29.37e6, "gather": 26.49e6, "pair": 3.18e6}}
+# Algorithmic work per unit for the roofline (the hot-path scope table's figures): flops per (particle,
+# window point) of the spread and of the gather, and per ordered pair within r_c of the pair correction;
+# forces + torques and forces only.
+FLOPS_POINT = {True: 22.0, False: 8.0}
+FLOPS_PAIR = {True: 250.0, False: 100.0}
 
 
 def workload(name="c2", n=None, h_ref=None):
@@ -470,8 +475,8 @@ def large_sweep(device, grids=(192, 256, 320), tol=1e-5, steps=3, warmup=2, seed
             assert h.check() == 0
         avg = {k: (v[0] / v[1] if v[1] else None) for k, v in stage.items()}
         MG = ch["M_G"]
-        flops = {"spread": 16.0 * n * MG ** 3, "gather": 16.0 * n * MG ** 3,
-                 "pair": 150.0 * n * (n / L ** 3 * 4.0 / 3.0 * math.pi * ch["r_c"] ** 3)}
+        flops = {"spread": FLOPS_POINT[True] * n * MG ** 3, "gather": FLOPS_POINT[True] * n * MG ** 3,
+                 "pair": FLOPS_PAIR[True] * n * (n / L ** 3 * 4.0 / 3.0 * math.pi * ch["r_c"] ** 3)}
         dom = max(flops, key=lambda k: avg[k] or 0.0)
         achieved = flops[dom] / (avg[dom] * 1e-3) / 1e12
         p64 = fcm.make_params(L, M, ch["Sigma"], ch["r_c"], MG, n, fcm.FCM_FP64)
@@ -785,8 +790,8 @@ def rigid_oracle_sample(tol, n_rods=16):
 
 
 def rigid_roofline(stages, n, M_G, device):
-    """FP32 ALU roofline of the spread inside the rigid solve: forces only, 12 flops per window point
-    (three components, two FMA each), against 152 SMs x 128 lanes x 2 x the maximum SM clock."""
+    """FP32 ALU roofline of the spread inside the rigid solve: forces only, 8 algorithmic flops per
+    window point, against 152 SMs x 128 lanes x 2 x the maximum SM clock."""
     import torch
     ms, cnt = stages.get("spread", (0.0, 0))
     if not cnt:
@@ -794,7 +799,7 @@ def rigid_roofline(stages, n, M_G, device):
     sm_count = torch.cuda.get_device_properties(device).multi_processor_count
     sm_max = peaks().get("sm_max_mhz") or 2070.0
     peak = sm_count * 128 * 2 * sm_max * 1e6 / 1e12
-    achieved = 12.0 * n * M_G ** 3 / (ms / cnt * 1e-3) / 1e12
+    achieved = FLOPS_POINT[False] * n * M_G ** 3 / (ms / cnt * 1e-3) / 1e12
     return {"bound": "alu", "kernel": "spread", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "spread_ms_per_launch": ms / cnt,
             "stage_share": {k: v[0] / sum(x[0] for kk, x in stages.items() if kk != "apply")
@@ -1237,9 +1242,9 @@ def main():
     avg = {name: (ms / cnt if cnt else None) for name, (ms, cnt) in stage.items()}
     per_launch = B if batched else 1        # systems one kernel launch processes
     pts = per_launch * n * w["M_G"] ** 3
-    flops = {"spread": 16.0 * pts, "gather": 16.0 * pts}
+    flops = {"spread": FLOPS_POINT[True] * pts, "gather": FLOPS_POINT[True] * pts}
     n_nb = n / w["L"] ** 3 * 4.0 / 3.0 * math.pi * w["r_c"] ** 3
-    flops["pair"] = 150.0 * per_launch * n * n_nb
+    flops["pair"] = FLOPS_PAIR[True] * per_launch * n * n_nb
     dominant = max(("spread", "gather", "pair"), key=lambda s: avg[s] or 0.0)
     achieved = flops[dominant] / (avg[dominant] * 1e-3) / 1e12
     traffic = TRAFFIC_BYTES.get(args.workload, {}).get(dominant)
