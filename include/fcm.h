@@ -75,11 +75,13 @@ typedef struct fcm_params {
   int precision;     /* fcm_precision                                                    */
   int max_n;         /* capacity: largest n accepted by fcm_apply                         */
   int tile[3];       /* FP32 spread/gather tile in grid points per dimension; 0 = choose */
-  int spread_kernel; /* FP32 spread: 0 = choose, 1 = row-stationary (registers, no      */
-                     /* atomics; needs tile[0] == 8 and M_G <= 16), 2 = shared atomics,  */
-                     /* 3 = tensor cores (tcgen05, TF32 operands split in three products */
-                     /* for FP32 accuracy; 8^3 tiles and M_G in {10, 12, 14}, otherwise  */
-                     /* as 0)                                                            */
+  int spread_kernel; /* FP32 spread: 0 = choose (the pencil kernel: register rows      */
+                     /* carried along x-pencils of tiles), 1 = row-stationary per pair   */
+                     /* of tiles (needs tile[0] == 8 and M_G <= 16), 2 = shared atomics, */
+                     /* 3 = tensor cores per pair of tiles, 4 = tensor cores along       */
+                     /* pencils (3 and 4: tcgen05 kind::tf32, operands split in three    */
+                     /* products for FP32 accuracy; 8^3 tiles and M_G in {10, 12, 14},   */
+                     /* 4 also Sigma_D == Sigma; otherwise as 0)                         */
 } fcm_params;
 
 typedef struct fcm_handle fcm_handle;

@@ -383,7 +383,7 @@ int validate(const fcm_params* p, std::string* why) {
   }
   if (p->precision != FCM_FP32 && p->precision != FCM_FP64) { *why = "precision must be FCM_FP32 or FCM_FP64"; return 0; }
   if (p->max_n < 0) { *why = "max_n must be >= 0"; return 0; }
-  if (p->spread_kernel < 0 || p->spread_kernel > 3) { *why = "spread_kernel must be 0, 1, 2 or 3"; return 0; }
+  if (p->spread_kernel < 0 || p->spread_kernel > 4) { *why = "spread_kernel must be 0, 1, 2, 3 or 4"; return 0; }
   return 1;
 }
 

@@ -341,7 +341,11 @@ int tile_smem_limit();
 // (fcm_params.spread_kernel).
 void launch_spread_f32(const Geometry<float>& g, const KernelConsts<float>& kc, bool torque, int spread_kernel,
                        const BinBuffers& b, float* grid, cudaStream_t s, long long* launches);
-// Tensor-core spread (spread_mma.cu): 8^3 tiles and M_G in {10, 12, 14}.
+// Tensor-core spread along x-pencils (spread_tc.cu): 8^3 tiles, M_G in {10, 12, 14}, Sigma_D = Sigma.
+bool spread_tc_eligible(const int tile[3], int MG, bool same_width);
+void launch_spread_tc(const Geometry<float>& g, const KernelConsts<float>& kc, bool torque, const BinBuffers& b,
+                      float* grid, cudaStream_t s);
+// Tensor-core spread per pair of tiles (spread_mma.cu): 8^3 tiles and M_G in {10, 12, 14}.
 bool spread_mma_eligible(const int tile[3], int MG);
 void launch_spread_mma(const Geometry<float>& g, const KernelConsts<float>& kc, bool torque, const BinBuffers& b,
                        float* grid, cudaStream_t s);

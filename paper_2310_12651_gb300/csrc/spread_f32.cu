@@ -809,7 +809,9 @@ static void atomic_variant(const Geometry<float>& g, const KernelConsts<float>& 
 
 void launch_spread_f32(const Geometry<float>& g, const KernelConsts<float>& kc, bool torque, int spread_kernel,
                        const BinBuffers& b, float* grid, cudaStream_t s, long long* launches) {
-  if (spread_kernel == 3 && spread_mma_eligible(g.tile, g.MG)) {
+  if (spread_kernel == 4 && spread_tc_eligible(g.tile, g.MG, !torque || kc.same_width)) {
+    launch_spread_tc(g, kc, torque, b, grid, s);
+  } else if (spread_kernel == 3 && spread_mma_eligible(g.tile, g.MG)) {
     launch_spread_mma(g, kc, torque, b, grid, s);
   } else if (rows_selected(g, spread_kernel) && spread_kernel != 1) {
 #define PENCIL_CALL(MGT, GUARD)                                                            \

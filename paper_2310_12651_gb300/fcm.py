@@ -156,8 +156,10 @@ def version() -> int:
 
 def make_params(L, M, Sigma, r_c, M_G, max_n, precision=FCM_FP32, a=1.0, eta=1.0, Sigma_D=0.0, tile=(0, 0, 0),
                 spread_kernel=0):
-    """fcm_params for fcm_create (include/fcm.h). spread_kernel: 0 = the library's choice, 1 = row-stationary,
-    2 = shared-memory atomics, 3 = tensor cores (8^3 tiles and M_G in {10, 12, 14}, otherwise as 0)."""
+    """fcm_params for fcm_create (include/fcm.h). spread_kernel: 0 = the library's choice (pencil kernel),
+    1 = row-stationary per pair of tiles, 2 = shared-memory atomics, 3 = tensor cores per pair of tiles,
+    4 = tensor cores along pencils (3, 4: 8^3 tiles and M_G in {10, 12, 14}, 4 also Sigma_D = Sigma;
+    otherwise as 0)."""
     p = Params()
     _check(_lib.fcm_params_default(ctypes.byref(p)))
     Ls = [float(L)] * 3 if not hasattr(L, "__len__") else [float(v) for v in L]

@@ -59,7 +59,7 @@ def test_fp32_torques_several_tiles(fcm, Sigma, M):
     assert_parity(W, Wo, FP32_TOL, f"W fp32 Sigma={Sigma}")
 
 
-@pytest.mark.parametrize("kernel", [0, 1, 2])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 4])
 def test_fp32_both_spread_kernels(fcm, kernel):
     """Pencil (0, the default), row-stationary per tile pair (1) and shared-atomic (2) spread kernels give
     the same product."""
@@ -113,6 +113,7 @@ def test_spread_grid_matches_oracle(fcm, precision):
     assert_parity(got, ref, FP32_TOL if precision == "fp32" else FP64_TOL, f"spread grid {precision}")
 
 
+@pytest.mark.parametrize("kernel", [0, 4])
 @pytest.mark.parametrize("M, Sigma, c_trunc, torques, sigma_d", [
     (42, 2.0, 4.7, True, 0.0),     # M_G = 14, M_x not a multiple of 4: scalar flushes; ragged last tile of 2 points
     (44, 1.5, 4.8, True, 0.0),     # M_G = 12, ragged last tile of 4 points
@@ -121,15 +122,16 @@ def test_spread_grid_matches_oracle(fcm, precision):
     (32, 1.2, 4.8, True, 1.5),     # Sigma_D != Sigma, M_G = 10 at h = 1.1
     (16, 2.0, 4.8, True, 0.0),     # M_G = 14: the extended row (21 points) wraps past M_x = 16
 ])
-def test_pencil_spread_grid_matches_oracle(fcm, M, Sigma, c_trunc, torques, sigma_d):
-    """The pencil spread's force density point by point: ragged and wrapping rows, the M_G variants, forces
-    only and a torque width different from Sigma."""
+def test_pencil_spread_grid_matches_oracle(fcm, M, Sigma, c_trunc, torques, sigma_d, kernel):
+    """The pencil spreads' force density point by point (0: register rows, 4: tensor cores, which falls back
+    to 0 for M_G = 16 and Sigma_D != Sigma): ragged and wrapping rows, the M_G variants, forces only and a
+    torque width different from Sigma."""
     torch = torch_cuda()
     n = max(200, int(0.05 * (M * 1.37) ** 3 / 4.19))
     s = suspension(n, 0.05, M, Sigma, 1e-6, 460 + M, torques=torques, c_trunc=c_trunc)
     s.Sigma_D = sigma_d
     SD = sigma_d if sigma_d else Sigma
-    p = fcm.make_params(s.L, s.M, s.Sigma, s.r_c, s.M_G, s.n, fcm.FCM_FP32, Sigma_D=sigma_d, spread_kernel=0)
+    p = fcm.make_params(s.L, s.M, s.Sigma, s.r_c, s.M_G, s.n, fcm.FCM_FP32, Sigma_D=sigma_d, spread_kernel=kernel)
     with fcm.Handle(p) as h:
         pos = torch.as_tensor(s.Y, dtype=torch.float32, device="cuda")
         F = torch.as_tensor(s.F, dtype=torch.float32, device="cuda")
