@@ -1070,6 +1070,7 @@ def main():
     ap.add_argument("--no-rigid", action="store_true", help="skip the rigid-rod mobility solve measurement")
     ap.add_argument("--no-large", action="store_true", help="skip the N = 1,048,576 sweep over 192^3-320^3 grids")
     ap.add_argument("--sweep-full", action="store_true", help="include the 12.8%% (N = 1.96M) sweep row")
+    ap.add_argument("--large-grids", default="192,256,320", help="grids of the N = 1,048,576 sweep (comma list)")
     ap.add_argument("--serve-requests", type=int, default=1024)
     ap.add_argument("--mode", default="batched", choices=["batched", "single"],
                     help="batched: one fcm_batch_apply over the stacked systems; single: one fcm_apply per system")
@@ -1094,7 +1095,7 @@ def main():
             if args.study == "crossover":
                 res = crossover_study(local)
             elif args.study == "large":
-                res = large_sweep(local)
+                res = large_sweep(local, grids=tuple(int(x) for x in args.large_grids.split(",")))
             else:
                 run = {"rigid": rigid_bench, "brownian": brownian_bench}[args.study]
                 res = run(local, with_oracle=not args.no_cpu_baseline)
@@ -1280,7 +1281,8 @@ def main():
     oracle_here = rank == 0 and world == 1 and not args.no_cpu_baseline
     brown = None if args.no_brownian else brownian_bench(local, with_oracle=oracle_here)
     rigid = None if args.no_rigid else rigid_bench(local, with_oracle=oracle_here)
-    large = None if (args.no_large or args.workload != "c2") else large_sweep(local)
+    large_grids = tuple(int(x) for x in args.large_grids.split(","))
+    large = None if (args.no_large or args.workload != "c2") else large_sweep(local, grids=large_grids)
 
     err = error_vs_oracle(local, oracle_jobs) if oracle_jobs is not None else None
 
