@@ -6,19 +6,23 @@
 // with x = Y_n - Y_m and the radial coefficients of the closed form, read from
 // piecewise-cubic tables built in FP64 (Taylor series for r < r_series, which
 // also covers coincident points), plus the self correction. Candidates come
-// from the 27 cells around n's cell (Section 4 step 1); cells adjacent in x are
-// contiguous in the cell-sorted arrays, so a warp walks at most 9 ranges (more
-// only where x wraps).
+// from the cells around n's cell (Section 4 step 1); cells adjacent in x are
+// contiguous in the cell-sorted arrays, so a CTA stages a few x ranges.
 //
-// GB300 decomposition: one CTA per pair cell stages the candidates of the 27
-// neighbour cells in shared memory; a warp takes one particle n at a time.
-// Lanes test 32 candidates at a time; the staged slots of hits are compacted
-// with a ballot into a per-warp shared-memory queue, and the correction is
-// evaluated when 32 hits are queued (each lane recomputes its pair's
-// separation from the staged position), so that work runs with every lane busy
-// although only ~15% of candidates are within r_c. Per-lane sums are
-// compensated (Kahan), the warp reduction is a tree, and the per-particle
-// totals over candidate chunks are compensated again (Neumaier).
+// GB300 decomposition: each unordered pair is evaluated once. The coefficients
+// depend on r only, so the partner's terms are the same expressions with
+// x -> -x (the odd cross-product terms change sign). One CTA per pair cell
+// stages its own cell and a half shell of 13 neighbour cells in shared memory;
+// a warp takes one particle n at a time and pairs it with the staged candidates
+// after its own slot. Lanes test 32 candidates at a time; the staged slots of
+// hits are compacted with a ballot into a per-warp shared-memory queue, and the
+// correction is evaluated when 32 hits are queued (each lane recomputes its
+// pair's separation from the staged position), so that work runs with every
+// lane busy although only ~15% of candidates are within r_c. n's sums are
+// compensated per lane (Kahan), reduced by a tree and compensated again across
+// candidate chunks (Neumaier); the partners' sums add up in shared memory and
+// reach the output with atomic adds, so the output is zeroed first and the
+// order of those additions is not fixed.
 #include "fcm_internal.cuh"
 
 namespace fcm {
@@ -44,50 +48,30 @@ __device__ inline float min_image(float d, float L) {
   return d;
 }
 
-template <bool TORQUE>
-__device__ inline void eval_pair(const PairConsts<float>& pc, const PairTable& tab, float4 dq, float4 Fj, float4 Tj,
-                                 Kahan* u, Kahan* w) {
-  float al, bt, cr, gm, dl;
-  pair_coeffs_table(dq.w, pc, tab, al, bt, cr, gm, dl);
-  const float dx = dq.x, dy = dq.y, dz = dq.z;
-  const float xF = dx * Fj.x + dy * Fj.y + dz * Fj.z;
-  float u0 = al * Fj.x + bt * xF * dx;
-  float u1 = al * Fj.y + bt * xF * dy;
-  float u2 = al * Fj.z + bt * xF * dz;
-  if (TORQUE) {
-    // U += cr (T x x)
-    u0 += cr * (Tj.y * dz - Tj.z * dy);
-    u1 += cr * (Tj.z * dx - Tj.x * dz);
-    u2 += cr * (Tj.x * dy - Tj.y * dx);
-    const float xT = dx * Tj.x + dy * Tj.y + dz * Tj.z;
-    // W += cr (F x x) + gm T + dl x (x.T)
-    w[0].add(cr * (Fj.y * dz - Fj.z * dy) + gm * Tj.x + dl * xT * dx);
-    w[1].add(cr * (Fj.z * dx - Fj.x * dz) + gm * Tj.y + dl * xT * dy);
-    w[2].add(cr * (Fj.x * dy - Fj.y * dx) + gm * Tj.z + dl * xT * dz);
-  }
-  u[0].add(u0);
-  u[1].add(u1);
-  u[2].add(u2);
-}
-
-// ---------------------------------------------------------------- cell-tiled kernel
+// ---------------------------------------------------------------- half-shell cell kernel
 //
-// One CTA per pair cell. The candidates of its 27 neighbour cells are staged
-// once in shared memory (positions, forces, torques; chunks of kCandChunk),
-// then each warp takes particles of the cell and runs the same ballot
-// compaction over the staged candidates: candidate reads are shared-memory
-// loads instead of L2 traffic repeated for every particle of the cell.
+// One CTA per pair cell c. Each unordered pair within r_c is evaluated once (the mobility
+// correction is symmetric: the pair's coefficients are shared, and the partner's terms follow
+// from x -> -x), so a CTA stages only its own cell and the 13 neighbour cells of a half shell:
+// offsets (dx, dy, dz) with dz = +1, or dz = 0 and dy = +1, or dz = dy = 0 and dx = +1. Every
+// unordered pair of neighbouring cells is met from exactly one side (m_i >= 3 keeps the offsets
+// distinct modulo m_i). The own cell is staged first in cell order, so particle i of the cell
+// pairs with the staged candidates after its own slot: same-cell pairs once, no self pair.
+// Terms for i add up in the lanes (compensated) and a warp reduction; terms for the partner j
+// add into per-candidate shared sums, which go to the output with global atomics after the
+// chunk; the output is zeroed before the launch.
 
 constexpr int kCellWarps = 8;
-constexpr int kCandChunk = 1280;   // above the 27-cell candidate count of the 5% suspension (about 1,025)
-static_assert(kCandChunk % 32 == 0, "candidate chunks are padded to whole 32-candidate passes");
+constexpr int kHalfChunk = 704;   // above the half-shell candidate count of the 5% suspension (about 530)
+static_assert(kHalfChunk % 32 == 0, "candidate chunks are padded to whole 32-candidate passes");
 constexpr int kIBatch = 128;
-constexpr int kMaxPieces = 18;
+constexpr int kMaxPieces = 12;
 
 template <bool TORQUE>
-constexpr size_t cell_kernel_smem() {
-  return sizeof(float4) * (size_t)kCandChunk * (TORQUE ? 3 : 2) + sizeof(float) * 12 * kIBatch +
-         sizeof(int) * kCellWarps * kQueue + sizeof(int) * 64 + sizeof(float4) * kMaxPieces;
+constexpr size_t half_kernel_smem() {
+  return sizeof(float4) * (size_t)kHalfChunk * (TORQUE ? 3 : 2) +
+         sizeof(float) * (size_t)kHalfChunk * (TORQUE ? 6 : 3) + sizeof(float) * 12 * kIBatch + sizeof(int) * kCellWarps * kQueue + sizeof(int) * 64 +
+         sizeof(float4) * kMaxPieces;
 }
 
 __device__ inline void neu_add(float* s, float* c, float v) {
@@ -97,7 +81,7 @@ __device__ inline void neu_add(float* s, float* c, float v) {
 }
 
 template <bool TORQUE, bool SHIFT>
-__global__ void __launch_bounds__(kCellWarps * 32, 3) pair_cell_kernel(Geometry<float> g, PairConsts<float> pc,
+__global__ void __launch_bounds__(kCellWarps * 32, 3) pair_half_kernel(Geometry<float> g, PairConsts<float> pc,
                                                                        PairTable tab,
                                                                        const float4* __restrict__ cpos,
                                                                        const float4* __restrict__ cF,
@@ -105,11 +89,13 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) pair_cell_kernel(Geometry<
                                                                        const int* __restrict__ cstart,
                                                                        float* __restrict__ Uo,
                                                                        float* __restrict__ Wo) {
+  constexpr int C = TORQUE ? 6 : 3;   // partner sums per candidate
   extern __shared__ float4 sm4[];
   float4* spos = sm4;
-  float4* sF = spos + kCandChunk;
-  float4* sT = sF + kCandChunk;
-  float* acc = reinterpret_cast<float*>(TORQUE ? sT + kCandChunk : sT);   // [kIBatch][12]
+  float4* sF = spos + kHalfChunk;
+  float4* sT = sF + kHalfChunk;
+  float* accj = reinterpret_cast<float*>(TORQUE ? sT + kHalfChunk : sT);   // [chunk][C]
+  float* acc = accj + C * kHalfChunk;                                       // [kIBatch][12]
   int* qj = reinterpret_cast<int*>(acc + 12 * kIBatch);                     // [warps][kQueue]
   int* meta = qj + kCellWarps * kQueue;                                     // pieces: source start, prefix
   float4* pshift = reinterpret_cast<float4*>(meta + 64);                    // periodic image shift per piece
@@ -125,28 +111,27 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) pair_cell_kernel(Geometry<
     const int lc = cell - cbase;
     const int cx = lc % mx, cy = (lc / mx) % my, cz = lc / (mx * my);
     int np = 0, total = 0;
-    for (int ddz = -1; ddz <= 1; ++ddz) {
-      const int zu = cz + ddz;
-      const int zc = pmod(zu, mz);
+    // cells xa .. xb of row (yu, zu) (unwrapped y, z; x wrapped by the caller), image shift sx
+    auto piece = [&](int yu, int zu, int xa, int xb, float sx) {
+      const float sy = yu < 0 ? -g.L[1] : (yu >= my ? g.L[1] : 0.f);
       const float sz = zu < 0 ? -g.L[2] : (zu >= mz ? g.L[2] : 0.f);
-      for (int ddy = -1; ddy <= 1; ++ddy) {
-        const int yu = cy + ddy;
-        const float sy = yu < 0 ? -g.L[1] : (yu >= my ? g.L[1] : 0.f);
-        const int rowbase = cbase + mx * (pmod(yu, my) + my * zc);
-        int ra[2], rb[2], k = 0;
-        float sx[2] = {0.f, 0.f};
-        if (cx - 1 >= 0 && cx + 1 < mx) { ra[0] = cx - 1; rb[0] = cx + 1; k = 1; }
-        else if (cx - 1 < 0) { ra[0] = mx - 1; rb[0] = mx - 1; sx[0] = -g.L[0]; ra[1] = 0; rb[1] = 1; k = 2; }
-        else { ra[0] = mx - 2; rb[0] = mx - 1; ra[1] = 0; rb[1] = 0; sx[1] = g.L[0]; k = 2; }
-        for (int q = 0; q < k; ++q) {
-          const int a = cstart[rowbase + ra[q]], b = cstart[rowbase + rb[q] + 1];
-          meta[2 * np] = a;
-          meta[2 * np + 1] = total;
-          pshift[np] = make_float4(sx[q], sy, sz, 0.f);
-          total += b - a;
-          ++np;
-        }
-      }
+      const int rowbase = cbase + mx * (pmod(yu, my) + my * pmod(zu, mz));
+      const int a = cstart[rowbase + xa], b = cstart[rowbase + xb + 1];
+      meta[2 * np] = a;
+      meta[2 * np + 1] = total;
+      pshift[np] = make_float4(sx, sy, sz, 0.f);
+      total += b - a;
+      ++np;
+    };
+    // the own cell and its +x neighbour
+    if (cx + 1 < mx) piece(cy, cz, cx, cx + 1, 0.f);
+    else { piece(cy, cz, cx, cx, 0.f); piece(cy, cz, 0, 0, g.L[0]); }
+    // rows dy = +1 at dz = 0, and dy = -1, 0, +1 at dz = +1: cells cx - 1 .. cx + 1
+    for (int r = 0; r < 4; ++r) {
+      const int yu = r == 0 ? cy + 1 : cy + r - 2, zu = r == 0 ? cz : cz + 1;
+      if (cx - 1 >= 0 && cx + 1 < mx) piece(yu, zu, cx - 1, cx + 1, 0.f);
+      else if (cx - 1 < 0) { piece(yu, zu, mx - 1, mx - 1, -g.L[0]); piece(yu, zu, 0, 1, 0.f); }
+      else { piece(yu, zu, mx - 2, mx - 1, 0.f); piece(yu, zu, 0, 0, g.L[0]); }
     }
     meta[2 * np + 1] = total;   // prefix sentinel
     meta[63] = np;
@@ -160,8 +145,8 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) pair_cell_kernel(Geometry<
   for (int ib = i_begin; ib < i_end; ib += kIBatch) {
     const int ni = min(kIBatch, i_end - ib);
     for (int k = threadIdx.x; k < 12 * ni; k += blockDim.x) acc[k] = 0.f;
-    for (int cb = 0; cb < total; cb += kCandChunk) {
-      const int nc = min(kCandChunk, total - cb);
+    for (int cb = 0; cb < total; cb += kHalfChunk) {
+      const int nc = min(kHalfChunk, total - cb);
       __syncthreads();
       for (int q = 0; q < npieces; ++q) {
         const int lo = max(meta[2 * q + 1], cb), hi = min(meta[2 * q + 3], cb + nc);
@@ -175,36 +160,73 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) pair_cell_kernel(Geometry<
           if (TORQUE) sT[lo - cb + k] = cT[src + k];
         }
       }
-      // pad to whole 32-candidate passes with far-away dummies (index -1): no bounds test in the loop
+      for (int k = threadIdx.x; k < C * nc; k += blockDim.x) accj[k] = 0.f;
+      // pad to whole 32-candidate passes with far-away dummies: no bounds test in the loop
       const int ncp = (nc + 31) & ~31;
       for (int k = nc + threadIdx.x; k < ncp; k += blockDim.x)
         spos[k] = make_float4(1e18f, 1e18f, 1e18f, __int_as_float(-1));
       __syncthreads();
       for (int il = warp; il < ni; il += kCellWarps) {
+        // candidates after particle i's own slot (the own cell is staged first, in cell order)
+        const int start = max(ib - i_begin + il + 1 - cb, 0);
+        if (start >= nc) continue;
         const float4 yi = cpos[ib + il];
-        const int self = __float_as_int(yi.w);
+        const float4 Fi = cF[ib + il];
+        const float4 Ti = TORQUE ? cT[ib + il] : make_float4(0.f, 0.f, 0.f, 0.f);
         Kahan u[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
         Kahan w[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-        // one queued hit: the separation is recomputed from the staged position
+        // one queued pair: the separation is recomputed from the staged position; i's terms go to
+        // the lane's sums, j's (x -> -x) to the candidate's shared sums
         auto eval_slot = [&](int jj) {
           const float4 yj = spos[jj];
-          float4 dq;
-          dq.x = SHIFT ? yi.x - yj.x : min_image(yi.x - yj.x, g.L[0]);
-          dq.y = SHIFT ? yi.y - yj.y : min_image(yi.y - yj.y, g.L[1]);
-          dq.z = SHIFT ? yi.z - yj.z : min_image(yi.z - yj.z, g.L[2]);
-          dq.w = fmaf(dq.x, dq.x, fmaf(dq.y, dq.y, dq.z * dq.z));
-          eval_pair<TORQUE>(pc, tab, dq, sF[jj], TORQUE ? sT[jj] : make_float4(0.f, 0.f, 0.f, 0.f), u, w);
-        };
-        int qn = 0;   // queued hits (the same in every lane); the queue starts at slot 0
-        for (int base = 0; base < ncp; base += 32) {
-          const float4 yj = spos[base + lane];
           const float dx = SHIFT ? yi.x - yj.x : min_image(yi.x - yj.x, g.L[0]);
           const float dy = SHIFT ? yi.y - yj.y : min_image(yi.y - yj.y, g.L[1]);
           const float dz = SHIFT ? yi.z - yj.z : min_image(yi.z - yj.z, g.L[2]);
-          const bool hit = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < pc.rc2 && __float_as_int(yj.w) != self;
+          float al, bt, cr, gm, dl;
+          pair_coeffs_table(fmaf(dx, dx, fmaf(dy, dy, dz * dz)), pc, tab, al, bt, cr, gm, dl);
+          const float4 Fj = sF[jj];
+          const float xFj = dx * Fj.x + dy * Fj.y + dz * Fj.z;
+          const float xFi = dx * Fi.x + dy * Fi.y + dz * Fi.z;
+          float ui0 = al * Fj.x + bt * xFj * dx, ui1 = al * Fj.y + bt * xFj * dy, ui2 = al * Fj.z + bt * xFj * dz;
+          float uj0 = al * Fi.x + bt * xFi * dx, uj1 = al * Fi.y + bt * xFi * dy, uj2 = al * Fi.z + bt * xFi * dz;
+          float* aj = accj + C * jj;
+          if (TORQUE) {
+            const float4 Tj = sT[jj];
+            // U_i += cr (T_j x x), U_j -= cr (T_i x x)
+            ui0 += cr * (Tj.y * dz - Tj.z * dy);
+            ui1 += cr * (Tj.z * dx - Tj.x * dz);
+            ui2 += cr * (Tj.x * dy - Tj.y * dx);
+            uj0 -= cr * (Ti.y * dz - Ti.z * dy);
+            uj1 -= cr * (Ti.z * dx - Ti.x * dz);
+            uj2 -= cr * (Ti.x * dy - Ti.y * dx);
+            // W_i += cr (F_j x x) + gm T_j + dl x (x.T_j), W_j += -cr (F_i x x) + gm T_i + dl x (x.T_i)
+            const float xTj = dx * Tj.x + dy * Tj.y + dz * Tj.z;
+            const float xTi = dx * Ti.x + dy * Ti.y + dz * Ti.z;
+            w[0].add(cr * (Fj.y * dz - Fj.z * dy) + gm * Tj.x + dl * xTj * dx);
+            w[1].add(cr * (Fj.z * dx - Fj.x * dz) + gm * Tj.y + dl * xTj * dy);
+            w[2].add(cr * (Fj.x * dy - Fj.y * dx) + gm * Tj.z + dl * xTj * dz);
+            atomicAdd(aj + 3, gm * Ti.x + dl * xTi * dx - cr * (Fi.y * dz - Fi.z * dy));
+            atomicAdd(aj + 4, gm * Ti.y + dl * xTi * dy - cr * (Fi.z * dx - Fi.x * dz));
+            atomicAdd(aj + 5, gm * Ti.z + dl * xTi * dz - cr * (Fi.x * dy - Fi.y * dx));
+          }
+          u[0].add(ui0);
+          u[1].add(ui1);
+          u[2].add(ui2);
+          atomicAdd(aj + 0, uj0);
+          atomicAdd(aj + 1, uj1);
+          atomicAdd(aj + 2, uj2);
+        };
+        int qn = 0;   // queued pairs (the same in every lane); the queue starts at slot 0
+        for (int base = start & ~31; base < ncp; base += 32) {
+          const int k = base + lane;
+          const float4 yj = spos[k];
+          const float dx = SHIFT ? yi.x - yj.x : min_image(yi.x - yj.x, g.L[0]);
+          const float dy = SHIFT ? yi.y - yj.y : min_image(yi.y - yj.y, g.L[1]);
+          const float dz = SHIFT ? yi.z - yj.z : min_image(yi.z - yj.z, g.L[2]);
+          const bool hit = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < pc.rc2 && k >= start;
           const unsigned m = __ballot_sync(kFullMask, hit);
           if (m == 0u) continue;
-          if (hit) myqj[qn + __popc(m & lt)] = base + lane;   // qn < 32 here, so the slot is < 64
+          if (hit) myqj[qn + __popc(m & lt)] = k;   // qn < 32 here, so the slot is < 64
           qn += __popc(m);
           if (qn >= 32) {
             __syncwarp();
@@ -230,6 +252,20 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) pair_cell_kernel(Geometry<
           for (int c = 0; c < 6; ++c) neu_add(a + c, a + 6 + c, r[c]);
         }
       }
+      __syncthreads();
+      // the partners' sums of this chunk to the output
+      for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+        const float* aj = accj + C * k;
+        const size_t o = 3 * (size_t)index_from_w(spos[k].w);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          if (aj[c] != 0.f) atomicAdd(Uo + o + c, aj[c]);
+        if (TORQUE && Wo) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            if (aj[3 + c] != 0.f) atomicAdd(Wo + o + c, aj[3 + c]);
+        }
+      }
     }
     __syncthreads();
     for (int il = threadIdx.x; il < ni; il += blockDim.x) {
@@ -237,14 +273,14 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) pair_cell_kernel(Geometry<
       const float* a = acc + 12 * il;
       const float4 Fi = cF[i];
       const size_t o = 3 * (size_t)index_from_w(cpos[i].w);
-      Uo[o + 0] = (a[0] + a[6]) + pc.selfVF * Fi.x;
-      Uo[o + 1] = (a[1] + a[7]) + pc.selfVF * Fi.y;
-      Uo[o + 2] = (a[2] + a[8]) + pc.selfVF * Fi.z;
+      atomicAdd(Uo + o + 0, (a[0] + a[6]) + pc.selfVF * Fi.x);
+      atomicAdd(Uo + o + 1, (a[1] + a[7]) + pc.selfVF * Fi.y);
+      atomicAdd(Uo + o + 2, (a[2] + a[8]) + pc.selfVF * Fi.z);
       if (TORQUE && Wo) {
         const float4 Ti = cT[i];
-        Wo[o + 0] = (a[3] + a[9]) + pc.selfWT * Ti.x;
-        Wo[o + 1] = (a[4] + a[10]) + pc.selfWT * Ti.y;
-        Wo[o + 2] = (a[5] + a[11]) + pc.selfWT * Ti.z;
+        atomicAdd(Wo + o + 0, (a[3] + a[9]) + pc.selfWT * Ti.x);
+        atomicAdd(Wo + o + 1, (a[4] + a[10]) + pc.selfWT * Ti.y);
+        atomicAdd(Wo + o + 2, (a[5] + a[11]) + pc.selfWT * Ti.z);
       }
     }
     __syncthreads();
@@ -252,10 +288,10 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) pair_cell_kernel(Geometry<
 }
 
 template <bool TORQUE, bool SHIFT>
-static void cell_variant(const Geometry<float>& g, const PairConsts<float>& pc, const PairTable& tab,
+static void half_variant(const Geometry<float>& g, const PairConsts<float>& pc, const PairTable& tab,
                          const BinBuffers& b, float* upair, float* wpair, cudaStream_t s) {
-  const size_t smem = cell_kernel_smem<TORQUE>();
-  auto k = pair_cell_kernel<TORQUE, SHIFT>;
+  const size_t smem = half_kernel_smem<TORQUE>();
+  auto k = pair_half_kernel<TORQUE, SHIFT>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k<<<b.ncells, kCellWarps * 32, smem, s>>>(g, pc, tab, (const float4*)b.c_pos, (const float4*)b.c_F,
                                             (const float4*)b.c_T, b.cell_start, upair, wpair);
@@ -264,12 +300,15 @@ static void cell_variant(const Geometry<float>& g, const PairConsts<float>& pc, 
 void launch_pair_f32(const Geometry<float>& g, const PairConsts<float>& pc, const PairTable& tab, bool torque,
                      const BinBuffers& b, int n, float* upair, float* wpair, cudaStream_t s, long long* launches) {
   if (n <= 0) return;
+  // every particle's sums arrive by atomic adds from its own CTA and its neighbours'
+  launch_zero(upair, sizeof(float) * 3 * (size_t)n, s, launches);
+  if (torque && wpair) launch_zero(wpair, sizeof(float) * 3 * (size_t)n, s, launches);
   if (torque) {
-    if (g.shift) cell_variant<true, true>(g, pc, tab, b, upair, wpair, s);
-    else cell_variant<true, false>(g, pc, tab, b, upair, wpair, s);
+    if (g.shift) half_variant<true, true>(g, pc, tab, b, upair, wpair, s);
+    else half_variant<true, false>(g, pc, tab, b, upair, wpair, s);
   } else {
-    if (g.shift) cell_variant<false, true>(g, pc, tab, b, upair, wpair, s);
-    else cell_variant<false, false>(g, pc, tab, b, upair, wpair, s);
+    if (g.shift) half_variant<false, true>(g, pc, tab, b, upair, wpair, s);
+    else half_variant<false, false>(g, pc, tab, b, upair, wpair, s);
   }
   *launches += 1;
 }
