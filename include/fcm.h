@@ -56,7 +56,8 @@ typedef enum fcm_status {
 typedef enum fcm_precision {
   FCM_FP32 = 0,  /* float I/O; tiled spread/gather, FP32 FFT; pair corrections from  */
                  /* piecewise cubics fitted in FP64 to the closed forms, a Taylor    */
-                 /* series below sigma/2, compensated per-particle pair sums         */
+                 /* series below sigma/2, per-particle pair sums compensated across  */
+                 /* candidate chunks                                                 */
   FCM_FP64 = 1   /* double I/O; the plain path: global FP64 atomics, FP64 FFT        */
 } fcm_precision;
 

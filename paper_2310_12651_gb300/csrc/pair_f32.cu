@@ -18,9 +18,10 @@
 // hits are compacted with a ballot into a per-warp shared-memory queue, and the
 // correction is evaluated when 32 hits are queued (each lane recomputes its
 // pair's separation from the staged position), so that work runs with every
-// lane busy although only ~15% of candidates are within r_c. n's sums are
-// compensated per lane (Kahan), reduced by a tree and compensated again across
-// candidate chunks (Neumaier); the partners' sums add up in shared memory and
+// lane busy although only ~15% of candidates are within r_c. n's sums add up
+// per lane (a lane sees about three of n's pairs), by a tree across the lanes
+// and compensated across candidate chunks (Neumaier); the partners' sums add
+// up in shared memory (one plane per component) and
 // reach the output with atomic adds, so the output is zeroed first and the
 // order of those additions is not fixed.
 #include "fcm_internal.cuh"
@@ -29,18 +30,6 @@ namespace fcm {
 
 constexpr unsigned kFullMask = 0xffffffffu;
 constexpr int kQueue = 64;
-
-// Compensated (Kahan) running sum: c carries the low-order part lost by s.
-struct Kahan {
-  float s, c;
-  __device__ inline void add(float v) {
-    const float y = v - c;
-    const float t = s + y;
-    c = (t - s) - y;
-    s = t;
-  }
-  __device__ inline float value() const { return s - c; }
-};
 
 __device__ inline float min_image(float d, float L) {
   if (d > 0.5f * L) d -= L;
@@ -57,7 +46,7 @@ __device__ inline float min_image(float d, float L) {
 // unordered pair of neighbouring cells is met from exactly one side (m_i >= 3 keeps the offsets
 // distinct modulo m_i). The own cell is staged first in cell order, so particle i of the cell
 // pairs with the staged candidates after its own slot: same-cell pairs once, no self pair.
-// Terms for i add up in the lanes (compensated) and a warp reduction; terms for the partner j
+// Terms for i add up in the lanes and a warp reduction; terms for the partner j
 // add into per-candidate shared sums, which go to the output with global atomics after the
 // chunk; the output is zeroed before the launch.
 
@@ -65,13 +54,13 @@ constexpr int kCellWarps = 8;
 constexpr int kHalfChunk = 704;   // above the half-shell candidate count of the 5% suspension (about 530)
 static_assert(kHalfChunk % 32 == 0, "candidate chunks are padded to whole 32-candidate passes");
 constexpr int kIBatch = 128;
-constexpr int kMaxPieces = 12;
+constexpr int kPieces = 10;   // x ranges staged per cell: 5 rows, each split in two where it wraps in x
 
 template <bool TORQUE>
 constexpr size_t half_kernel_smem() {
   return sizeof(float4) * (size_t)kHalfChunk * (TORQUE ? 3 : 2) +
          sizeof(float) * (size_t)kHalfChunk * (TORQUE ? 6 : 3) + sizeof(float) * 12 * kIBatch + sizeof(int) * kCellWarps * kQueue + sizeof(int) * 64 +
-         sizeof(float4) * kMaxPieces;
+         sizeof(float4) * kPieces;
 }
 
 __device__ inline void neu_add(float* s, float* c, float v) {
@@ -94,7 +83,7 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) pair_half_kernel(Geometry<
   float4* spos = sm4;
   float4* sF = spos + kHalfChunk;
   float4* sT = sF + kHalfChunk;
-  float* accj = reinterpret_cast<float*>(TORQUE ? sT + kHalfChunk : sT);   // [chunk][C]
+  float* accj = reinterpret_cast<float*>(TORQUE ? sT + kHalfChunk : sT);   // [C][chunk]
   float* acc = accj + C * kHalfChunk;                                       // [kIBatch][12]
   int* qj = reinterpret_cast<int*>(acc + 12 * kIBatch);                     // [warps][kQueue]
   int* meta = qj + kCellWarps * kQueue;                                     // pieces: source start, prefix
@@ -105,39 +94,53 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) pair_half_kernel(Geometry<
   if (i_begin >= i_end) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int mx = g.mcell[0], my = g.mcell[1], mz = g.mcell[2];
-  if (threadIdx.x == 0) {
+  if (warp == 0) {
+    // kPieces slots, lane l describes slot l: row l / 2, part l % 2 of a row that wraps in x. Row 0 is
+    // the own cell and its +x neighbour (the own cell first); rows 1 .. 4 are dy = +1 at dz = 0 and
+    // dy = -1, 0, +1 at dz = +1, cells cx - 1 .. cx + 1. A slot a row does not need stays empty.
     const int cs = g.nsys > 1 ? cell / g.cells_per : 0;   // system of this cell (batched launches)
     const int cbase = cs * g.cells_per;
     const int lc = cell - cbase;
     const int cx = lc % mx, cy = (lc / mx) % my, cz = lc / (mx * my);
-    int np = 0, total = 0;
-    // cells xa .. xb of row (yu, zu) (unwrapped y, z; x wrapped by the caller), image shift sx
-    auto piece = [&](int yu, int zu, int xa, int xb, float sx) {
-      const float sy = yu < 0 ? -g.L[1] : (yu >= my ? g.L[1] : 0.f);
-      const float sz = zu < 0 ? -g.L[2] : (zu >= mz ? g.L[2] : 0.f);
-      const int rowbase = cbase + mx * (pmod(yu, my) + my * pmod(zu, mz));
-      const int a = cstart[rowbase + xa], b = cstart[rowbase + xb + 1];
-      meta[2 * np] = a;
-      meta[2 * np + 1] = total;
-      pshift[np] = make_float4(sx, sy, sz, 0.f);
-      total += b - a;
-      ++np;
-    };
-    // the own cell and its +x neighbour
-    if (cx + 1 < mx) piece(cy, cz, cx, cx + 1, 0.f);
-    else { piece(cy, cz, cx, cx, 0.f); piece(cy, cz, 0, 0, g.L[0]); }
-    // rows dy = +1 at dz = 0, and dy = -1, 0, +1 at dz = +1: cells cx - 1 .. cx + 1
-    for (int r = 0; r < 4; ++r) {
-      const int yu = r == 0 ? cy + 1 : cy + r - 2, zu = r == 0 ? cz : cz + 1;
-      if (cx - 1 >= 0 && cx + 1 < mx) piece(yu, zu, cx - 1, cx + 1, 0.f);
-      else if (cx - 1 < 0) { piece(yu, zu, mx - 1, mx - 1, -g.L[0]); piece(yu, zu, 0, 1, 0.f); }
-      else { piece(yu, zu, mx - 2, mx - 1, 0.f); piece(yu, zu, 0, 0, g.L[0]); }
+    const int r = lane >> 1, part = lane & 1;
+    int xa = 0, xb = -1;   // cells xa .. xb of the row; empty when xb < xa
+    float sx = 0.f;
+    if (r == 0) {
+      if (part == 0) { xa = cx; xb = (cx + 1 < mx) ? cx + 1 : cx; }
+      else if (cx + 1 >= mx) { xa = 0; xb = 0; sx = g.L[0]; }
+    } else if (r < 5) {
+      if (cx - 1 >= 0 && cx + 1 < mx) { if (part == 0) { xa = cx - 1; xb = cx + 1; } }
+      else if (cx - 1 < 0) {
+        if (part == 0) { xa = mx - 1; xb = mx - 1; sx = -g.L[0]; } else { xa = 0; xb = 1; }
+      } else {
+        if (part == 0) { xa = mx - 2; xb = mx - 1; } else { xa = 0; xb = 0; sx = g.L[0]; }
+      }
     }
-    meta[2 * np + 1] = total;   // prefix sentinel
-    meta[63] = np;
+    const int yu = r == 1 ? cy + 1 : cy + r - 3, zu = r <= 1 ? cz : cz + 1;   // row 0: (cy, cz)
+    const int yr = r == 0 ? cy : yu;
+    int a = 0, cnt = 0;
+    if (lane < kPieces && xb >= xa) {
+      const int rowbase = cbase + mx * (pmod(yr, my) + my * pmod(zu, mz));
+      a = cstart[rowbase + xa];
+      cnt = cstart[rowbase + xb + 1] - a;
+    }
+    int pre = cnt;   // inclusive prefix over the slots
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(kFullMask, pre, o);
+      if (lane >= o) pre += v;
+    }
+    if (lane < kPieces) {
+      meta[2 * lane] = a;
+      meta[2 * lane + 1] = pre - cnt;
+      const float sy = yr < 0 ? -g.L[1] : (yr >= my ? g.L[1] : 0.f);
+      const float sz = zu < 0 ? -g.L[2] : (zu >= mz ? g.L[2] : 0.f);
+      pshift[lane] = make_float4(sx, sy, sz, 0.f);
+    }
+    if (lane == kPieces - 1) meta[2 * kPieces + 1] = pre;   // prefix sentinel
   }
   __syncthreads();
-  const int npieces = meta[63];
+  constexpr int npieces = kPieces;
   const int total = meta[2 * npieces + 1];
   const unsigned lt = (1u << lane) - 1u;
   int* myqj = qj + warp * kQueue;
@@ -160,7 +163,7 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) pair_half_kernel(Geometry<
           if (TORQUE) sT[lo - cb + k] = cT[src + k];
         }
       }
-      for (int k = threadIdx.x; k < C * nc; k += blockDim.x) accj[k] = 0.f;
+      for (int k = threadIdx.x; k < C * kHalfChunk; k += blockDim.x) accj[k] = 0.f;
       // pad to whole 32-candidate passes with far-away dummies: no bounds test in the loop
       const int ncp = (nc + 31) & ~31;
       for (int k = nc + threadIdx.x; k < ncp; k += blockDim.x)
@@ -173,8 +176,7 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) pair_half_kernel(Geometry<
         const float4 yi = cpos[ib + il];
         const float4 Fi = cF[ib + il];
         const float4 Ti = TORQUE ? cT[ib + il] : make_float4(0.f, 0.f, 0.f, 0.f);
-        Kahan u[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-        Kahan w[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        float u[3] = {0.f, 0.f, 0.f}, w[3] = {0.f, 0.f, 0.f};
         // one queued pair: the separation is recomputed from the staged position; i's terms go to
         // the lane's sums, j's (x -> -x) to the candidate's shared sums
         auto eval_slot = [&](int jj) {
@@ -189,7 +191,7 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) pair_half_kernel(Geometry<
           const float xFi = dx * Fi.x + dy * Fi.y + dz * Fi.z;
           float ui0 = al * Fj.x + bt * xFj * dx, ui1 = al * Fj.y + bt * xFj * dy, ui2 = al * Fj.z + bt * xFj * dz;
           float uj0 = al * Fi.x + bt * xFi * dx, uj1 = al * Fi.y + bt * xFi * dy, uj2 = al * Fi.z + bt * xFi * dz;
-          float* aj = accj + C * jj;
+          float* aj = accj + jj;   // component c at aj[c kHalfChunk]
           if (TORQUE) {
             const float4 Tj = sT[jj];
             // U_i += cr (T_j x x), U_j -= cr (T_i x x)
@@ -202,19 +204,19 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) pair_half_kernel(Geometry<
             // W_i += cr (F_j x x) + gm T_j + dl x (x.T_j), W_j += -cr (F_i x x) + gm T_i + dl x (x.T_i)
             const float xTj = dx * Tj.x + dy * Tj.y + dz * Tj.z;
             const float xTi = dx * Ti.x + dy * Ti.y + dz * Ti.z;
-            w[0].add(cr * (Fj.y * dz - Fj.z * dy) + gm * Tj.x + dl * xTj * dx);
-            w[1].add(cr * (Fj.z * dx - Fj.x * dz) + gm * Tj.y + dl * xTj * dy);
-            w[2].add(cr * (Fj.x * dy - Fj.y * dx) + gm * Tj.z + dl * xTj * dz);
-            atomicAdd(aj + 3, gm * Ti.x + dl * xTi * dx - cr * (Fi.y * dz - Fi.z * dy));
-            atomicAdd(aj + 4, gm * Ti.y + dl * xTi * dy - cr * (Fi.z * dx - Fi.x * dz));
-            atomicAdd(aj + 5, gm * Ti.z + dl * xTi * dz - cr * (Fi.x * dy - Fi.y * dx));
+            w[0] += (cr * (Fj.y * dz - Fj.z * dy) + gm * Tj.x + dl * xTj * dx);
+            w[1] += (cr * (Fj.z * dx - Fj.x * dz) + gm * Tj.y + dl * xTj * dy);
+            w[2] += (cr * (Fj.x * dy - Fj.y * dx) + gm * Tj.z + dl * xTj * dz);
+            atomicAdd(aj + 3 * kHalfChunk, gm * Ti.x + dl * xTi * dx - cr * (Fi.y * dz - Fi.z * dy));
+            atomicAdd(aj + 4 * kHalfChunk, gm * Ti.y + dl * xTi * dy - cr * (Fi.z * dx - Fi.x * dz));
+            atomicAdd(aj + 5 * kHalfChunk, gm * Ti.z + dl * xTi * dz - cr * (Fi.x * dy - Fi.y * dx));
           }
-          u[0].add(ui0);
-          u[1].add(ui1);
-          u[2].add(ui2);
-          atomicAdd(aj + 0, uj0);
-          atomicAdd(aj + 1, uj1);
-          atomicAdd(aj + 2, uj2);
+          u[0] += ui0;
+          u[1] += ui1;
+          u[2] += ui2;
+          atomicAdd(aj + 0 * kHalfChunk, uj0);
+          atomicAdd(aj + 1 * kHalfChunk, uj1);
+          atomicAdd(aj + 2 * kHalfChunk, uj2);
         };
         int qn = 0;   // queued pairs (the same in every lane); the queue starts at slot 0
         for (int base = start & ~31; base < ncp; base += 32) {
@@ -240,7 +242,7 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) pair_half_kernel(Geometry<
         __syncwarp();
         if (lane < qn) eval_slot(myqj[lane]);
         __syncwarp();
-        float r[6] = {u[0].value(), u[1].value(), u[2].value(), w[0].value(), w[1].value(), w[2].value()};
+        float r[6] = {u[0], u[1], u[2], w[0], w[1], w[2]};
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
@@ -255,15 +257,15 @@ __global__ void __launch_bounds__(kCellWarps * 32, 3) pair_half_kernel(Geometry<
       __syncthreads();
       // the partners' sums of this chunk to the output
       for (int k = threadIdx.x; k < nc; k += blockDim.x) {
-        const float* aj = accj + C * k;
+        const float* aj = accj + k;
         const size_t o = 3 * (size_t)index_from_w(spos[k].w);
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-          if (aj[c] != 0.f) atomicAdd(Uo + o + c, aj[c]);
+          if (aj[c * kHalfChunk] != 0.f) atomicAdd(Uo + o + c, aj[c * kHalfChunk]);
         if (TORQUE && Wo) {
 #pragma unroll
           for (int c = 0; c < 3; ++c)
-            if (aj[3 + c] != 0.f) atomicAdd(Wo + o + c, aj[3 + c]);
+            if (aj[(3 + c) * kHalfChunk] != 0.f) atomicAdd(Wo + o + c, aj[(3 + c) * kHalfChunk]);
         }
       }
     }
