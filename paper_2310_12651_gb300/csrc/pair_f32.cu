@@ -51,16 +51,17 @@ __device__ inline float min_image(float d, float L) {
 // chunk; the output is zeroed before the launch.
 
 constexpr int kCellWarps = 8;
-constexpr int kHalfChunk = 704;   // above the half-shell candidate count of the 5% suspension (about 530)
+constexpr int kHalfChunk = 640;   // above the half-shell candidate count of the 5% suspension (about 530)
 static_assert(kHalfChunk % 32 == 0, "candidate chunks are padded to whole 32-candidate passes");
-constexpr int kIBatch = 128;
+constexpr int kIBatch = 64;      // particles of a cell per pass (a cell holds about 38 at 5%)
+// 51.6 KB of shared memory and at most 64 registers per thread: four 256-thread CTAs per SM
 constexpr int kPieces = 10;   // x ranges staged per cell: 5 rows, each split in two where it wraps in x
 
 template <bool TORQUE>
 constexpr size_t half_kernel_smem() {
   return sizeof(float4) * (size_t)kHalfChunk * (TORQUE ? 3 : 2) +
-         sizeof(float) * (size_t)kHalfChunk * (TORQUE ? 6 : 3) + sizeof(float) * 12 * kIBatch + sizeof(int) * kCellWarps * kQueue + sizeof(int) * 64 +
-         sizeof(float4) * kPieces;
+         sizeof(float) * (size_t)kHalfChunk * (TORQUE ? 6 : 3) + sizeof(float) * 12 * kIBatch +
+         sizeof(int) * kCellWarps * kQueue + sizeof(int) * 64 + sizeof(float4) * kPieces;
 }
 
 __device__ inline void neu_add(float* s, float* c, float v) {
@@ -70,7 +71,7 @@ __device__ inline void neu_add(float* s, float* c, float v) {
 }
 
 template <bool TORQUE, bool SHIFT>
-__global__ void __launch_bounds__(kCellWarps * 32, 3) pair_half_kernel(Geometry<float> g, PairConsts<float> pc,
+__global__ void __launch_bounds__(kCellWarps * 32, 4) pair_half_kernel(Geometry<float> g, PairConsts<float> pc,
                                                                        PairTable tab,
                                                                        const float4* __restrict__ cpos,
                                                                        const float4* __restrict__ cF,
