@@ -270,12 +270,16 @@ __global__ void __launch_bounds__(rows_threads(MGT), 1) spread_rows_kernel(Geome
 // points). Forces only: f_c(x) += G F'_c (P g + B d^2 g). Sigma_D != Sigma keeps the torque terms on
 // their own profiles d g_D and g_D with the row factor H = tq g_D(dy) g_D(dz).
 
+// Particles staged per pass of the pencil kernel. The profile tables are double-buffered: while
+// the row updates of pass c read one table set, the same threads build the tables of pass c + 1 in
+// the other (a warp whose rows finish early starts on them at once), and the raw rows (position,
+// force, torque) of pass c + 2 arrive by asynchronous copies. One CTA barrier per pass. Passes of
+// 128 particles where both table sets fit shared memory (one width and M_G <= 14), else 64.
 enum { kPencilForces = 0, kPencilSameWidth = 1, kPencilTwoWidths = 2 };
 
-// Particles staged per pass of the pencil kernel. Their raw rows (position, force, torque) are
-// fetched into a second buffer with asynchronous copies while the previous pass runs, so building
-// the profile tables reads shared memory only.
-constexpr int kPencilChunk = 128;
+__host__ __device__ constexpr int pencil_chunk(int MGT, int MODE) {
+  return (MODE != kPencilTwoWidths && MGT <= 14) ? 128 : 64;
+}
 
 // Register pairs of a pencil row: window pairs start at pair ox / 2 with ox in [0, 8).
 __host__ __device__ constexpr int pencil_pairs(int MGT) { return row_pairs(MGT) + 3; }
@@ -289,50 +293,59 @@ struct PencilTables {
   float4* pf;   // [chunk] F' = nrm F (two widths: F)
   float4* pt;   // [chunk] U' = tq T (two widths: T)
   int4* po;     // [chunk] (x offset in the tile, y and z window start in the region, tile step)
-  float4* raw;  // [2][3][chunk] raw rows: position, force, torque (double buffer)
   float* xk;    // two widths: [chunk][4 NK] d g_D along x, two pairs per float4
   float* xd;    // two widths: [chunk][2 NP] g_D along x
 };
 
-template <int MGT>
-__device__ inline PencilTables pencil_tables(float4* sm) {
+// float4 of one table set: the float4 tables, then (two widths) the float tables rounded up.
+__host__ __device__ constexpr int pencil_set_f4(int MGT, int MODE) {
+  return pencil_chunk(MGT, MODE) * (2 * row_pairs(MGT) + 2 * MGT + 3) +
+         (MODE == kPencilTwoWidths
+              ? (pencil_chunk(MGT, MODE) * (4 * ((row_pairs(MGT) + 1) / 2) + 2 * row_pairs(MGT)) + 3) / 4
+              : 0);
+}
+
+// Table set t (0 or 1); the raw rows [2][3][chunk] follow both sets.
+template <int MGT, int MODE>
+__device__ inline PencilTables pencil_tables(float4* sm, int t) {
   constexpr int NP = row_pairs(MGT), NK = (NP + 1) / 2;
-  constexpr int C = kPencilChunk;
-  PencilTables t;
-  t.xa = sm;
-  t.xb = t.xa + C * NP;
-  t.yt = t.xb + C * NP;
-  t.zt = t.yt + C * MGT;
-  t.pf = t.zt + C * MGT;
-  t.pt = t.pf + C;
-  t.po = reinterpret_cast<int4*>(t.pt + C);
-  t.raw = reinterpret_cast<float4*>(t.po + C);
-  t.xk = reinterpret_cast<float*>(t.raw + 6 * C);
-  t.xd = t.xk + C * 4 * NK;
-  return t;
+  constexpr int C = pencil_chunk(MGT, MODE);
+  PencilTables s;
+  s.xa = sm + (size_t)t * pencil_set_f4(MGT, MODE);
+  s.xb = s.xa + C * NP;
+  s.yt = s.xb + C * NP;
+  s.zt = s.yt + C * MGT;
+  s.pf = s.zt + C * MGT;
+  s.pt = s.pf + C;
+  s.po = reinterpret_cast<int4*>(s.pt + C);
+  s.xk = reinterpret_cast<float*>(s.po + C);
+  s.xd = s.xk + C * 4 * NK;
+  return s;
 }
 
-__host__ __device__ constexpr size_t pencil_tables_bytes(int MGT) {
-  return sizeof(float4) * (size_t)kPencilChunk * (2 * row_pairs(MGT) + 2 * MGT + 3 + 6 + (row_pairs(MGT) + 1) / 2) +
-         sizeof(float) * (size_t)kPencilChunk * 2 * row_pairs(MGT);
+template <int MGT, int MODE>
+__device__ inline float4* pencil_raw(float4* sm, int buf) {
+  return sm + 2 * (size_t)pencil_set_f4(MGT, MODE) + (size_t)buf * 3 * pencil_chunk(MGT, MODE);
 }
 
-// Asynchronous 16-byte copy global -> shared (the raw rows of the next pass).
+__host__ __device__ constexpr size_t pencil_tables_bytes(int MGT, int MODE) {
+  return sizeof(float4) * (2 * (size_t)pencil_set_f4(MGT, MODE) + 6 * (size_t)pencil_chunk(MGT, MODE));
+}
+
+// Asynchronous 16-byte copy global -> shared (the raw rows of a later pass).
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
 }
 
-// Raw rows of particles [base, base + np) into buffer `buf`.
-template <bool TORQUE>
-__device__ __forceinline__ void pencil_fetch(const PencilTables& tb, int buf, int base, int np,
-                                             const float4* __restrict__ pos, const float4* __restrict__ Fv,
-                                             const float4* __restrict__ Tv) {
-  float4* r = tb.raw + (size_t)buf * 3 * kPencilChunk;
+// Raw rows of particles [base, base + np) into raw buffer r ([3][C]).
+template <bool TORQUE, int C>
+__device__ __forceinline__ void pencil_fetch(float4* r, int base, int np, const float4* __restrict__ pos,
+                                             const float4* __restrict__ Fv, const float4* __restrict__ Tv) {
   for (int k = threadIdx.x; k < (TORQUE ? 3 : 2) * np; k += blockDim.x) {
-    const int a = k / np, q = k - a * np;
+    const int a = k >= 2 * np ? 2 : (k >= np ? 1 : 0), q = k - a * np;
     const float4* src = (a == 0 ? pos : (a == 1 ? Fv : Tv)) + base + q;
-    cp_async16(r + a * kPencilChunk + q, src);
+    cp_async16(r + a * C + q, src);
   }
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
@@ -454,20 +467,12 @@ __global__ void __launch_bounds__(rows_threads(MGT), 1) spread_pencil_kernel(Geo
     sy[k] = make_float2(0.f, 0.f);
     sz[k] = make_float2(0.f, 0.f);
   }
-  const PencilTables tb = pencil_tables<MGT>(sm4);
   int cur = 0;   // tile step whose x origin anchors the register row
-
-  pencil_fetch<TORQUE>(tb, 0, p_begin, min(kPencilChunk, p_end - p_begin), pos, Fv, Tv);
-  int buf = 0;
-  for (int base = p_begin; base < p_end; base += kPencilChunk, buf ^= 1) {
-    const int np = min(kPencilChunk, p_end - base);
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    __syncthreads();   // this pass's raw rows are in; every warp is done with the previous tables
-    if (base + np < p_end)
-      pencil_fetch<TORQUE>(tb, buf ^ 1, base + np, min(kPencilChunk, p_end - base - np), pos, Fv, Tv);
-    const float4* rpos = tb.raw + (size_t)buf * 3 * kPencilChunk;
-    const float4* rF = rpos + kPencilChunk;
-    const float4* rT = rF + kPencilChunk;
+  constexpr int C = pencil_chunk(MGT, MODE);
+  // profile tables of one pass (particles [base, base + np)) from its raw rows
+  auto build = [&](const PencilTables& tb, const float4* rpos, int np) {
+    const float4* rF = rpos + C;
+    const float4* rT = rF + C;
     // y and z profiles {g, d, A + B d^2 (y) or B d^2 (z), g_D}
     for (int k = threadIdx.x; k < np * 2 * MGT; k += blockDim.x) {
       const int q = k / (2 * MGT);
@@ -539,7 +544,21 @@ __global__ void __launch_bounds__(rows_threads(MGT), 1) spread_pencil_kernel(Geo
         tb.pt[q] = make_float4(kc.tq * t.x, kc.tq * t.y, kc.tq * t.z, 0.f);
       }
     }
-    __syncthreads();
+  };
+  const int npass = (p_end - p_begin + C - 1) / C;
+  pencil_fetch<TORQUE, C>(pencil_raw<MGT, MODE>(sm4, 0), p_begin, min(C, p_end - p_begin), pos, Fv, Tv);
+  if (npass > 1) pencil_fetch<TORQUE, C>(pencil_raw<MGT, MODE>(sm4, 1), p_begin + C, min(C, p_end - p_begin - C), pos, Fv, Tv);
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncthreads();
+  build(pencil_tables<MGT, MODE>(sm4, 0), pencil_raw<MGT, MODE>(sm4, 0), min(C, p_end - p_begin));
+  __syncthreads();
+  for (int pass = 0; pass < npass; ++pass) {
+    const int base = p_begin + pass * C;
+    const int np = min(C, p_end - base);
+    // raw rows of pass + 2 into the buffer that pass's tables were built from
+    if (pass + 2 < npass)
+      pencil_fetch<TORQUE, C>(pencil_raw<MGT, MODE>(sm4, pass & 1), base + 2 * C, min(C, p_end - base - 2 * C), pos, Fv, Tv);
+    const PencilTables tb = pencil_tables<MGT, MODE>(sm4, pass & 1);
     for (int q = 0; q < np; ++q) {
       const int4 off = tb.po[q];
       // the walk reaches the particle's tile: complete points of the passed tiles go to the grid
@@ -611,6 +630,11 @@ __global__ void __launch_bounds__(rows_threads(MGT), 1) spread_pencil_kernel(Geo
       }
 #undef FCM_PENCIL_CASE
     }
+    // tables of the next pass, into the set the previous pass used
+    if (pass + 1 < npass)
+      build(pencil_tables<MGT, MODE>(sm4, (pass + 1) & 1), pencil_raw<MGT, MODE>(sm4, (pass + 1) & 1), min(C, p_end - base - C));
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();   // the next tables and the raw rows of pass + 2 are in; this pass's tables are free
   }
   if (has_row) {   // the last tile reached: every pair of the register row, x from 8 cur on
     const size_t Mtot = (size_t)g.M[0] * g.M[1] * g.M[2];
@@ -756,7 +780,7 @@ static bool rows_selected(const Geometry<float>& g, int spread_kernel) {
 template <int MGT, bool GUARD, int MODE>
 static void pencil_variant(const Geometry<float>& g, const KernelConsts<float>& kc, const BinBuffers& b, float* grid,
                            cudaStream_t s) {
-  const size_t smem = pencil_tables_bytes(MGT);
+  const size_t smem = pencil_tables_bytes(MGT, MODE);
   const int threads = (((g.tile[1] + g.MG - 1) * (g.tile[2] + g.MG - 1) + 31) / 32) * 32;
   const int nsys = g.nsys > 1 ? g.nsys : 1;
   const int blocks = nsys * g.ntile[1] * g.ntile[2];
@@ -768,7 +792,9 @@ static void pencil_variant(const Geometry<float>& g, const KernelConsts<float>& 
 
 size_t spread_smem_bytes(const int tile[3], int MG) {
   if (!spread_uses_rows(tile, MG)) return tile_smem_bytes(tile, MG);
-  const size_t tab = std::max(row_tables_bytes(rows_mgt(MG)), pencil_tables_bytes(rows_mgt(MG)));
+  const size_t tab = std::max(row_tables_bytes(rows_mgt(MG)),
+                              std::max(pencil_tables_bytes(rows_mgt(MG), kPencilSameWidth),
+                                       pencil_tables_bytes(rows_mgt(MG), kPencilTwoWidths)));
   const size_t ext = tile_smem_bytes(tile, MG);
   return tab > ext ? tab : ext;  // any of the kernels may be selected for this tile
 }
