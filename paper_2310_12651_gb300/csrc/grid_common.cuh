@@ -90,27 +90,32 @@ __device__ inline int4 window_offset(const Geometry<float>& g, const TileOrigin&
 // plane, rounded up to 8 bytes.
 __host__ __device__ inline int yz_plane_offset(const ExtLayout& l) { return (l.C + 1) & ~1; }
 
-// Copies the extended region of the grid (3 components) into shared memory with
-// asynchronous 4-byte copies: warps take (component, z) planes, lanes take x,
-// rows advance by pointer increments (the y range is split at its periodic wrap,
-// so no per-row wrap test). Layout: the x component as one plane (index
-// ez Q + ey P + ex), then the y and z components interleaved as float2 at the
-// same index from yz_plane_offset, so the gather reads them with one 8-byte load.
+// Copies z planes [pa, pb) of the extended region of the grid (3 components) into shared memory
+// with asynchronous 4-byte copies: warps take (component, z) planes, lanes take x, rows advance by
+// pointer increments (the y range is split at its periodic wrap, so no per-row wrap test). Plane
+// ez is taken at grid z = o.oz0 + ez and goes to plane slot ez mod E_Z, so a CTA that walks a
+// z-pencil of tiles keeps the region as a ring of E_Z planes and copies only the planes a step
+// adds (pa, pb may exceed E_Z there; the default copies the whole region). Layout: the x component
+// as one plane (index slot Q + ey P + ex), then the y and z components interleaved as float2 at
+// the same index from yz_plane_offset, so the gather reads them with one 8-byte load.
 __device__ inline void stage_region_async(const Geometry<float>& g, const TileOrigin& o, const ExtLayout& l,
-                                          const float* __restrict__ grid, float* ext) {
+                                          const float* __restrict__ grid, float* ext, int pa = 0, int pb = -1) {
+  if (pb < 0) pb = l.EZ;
   const size_t Mtot = (size_t)g.M[0] * g.M[1] * g.M[2];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  if (lane < l.EX) {
+  const int np = pb - pa;
+  if (lane < l.EX && np > 0) {
     const int gx = wrap_index(o.ox0 + lane, g.M[0]);
     const int gy0 = wrap_index(o.oy0, g.M[1]);
     const int n1 = min(l.EY, g.M[1] - gy0);   // rows before the periodic wrap in y
     const size_t row = (size_t)g.M[0];
-    for (int pl = warp; pl < 3 * l.EZ; pl += nwarp) {
-      const int c = pl / l.EZ;
-      const int ez = pl - c * l.EZ;
+    for (int pl = warp; pl < 3 * np; pl += nwarp) {
+      const int c = pl >= 2 * np ? 2 : (pl >= np ? 1 : 0);
+      const int ez = pa + (pl - c * np);
       const int gz = wrap_index(o.oz0 + ez, g.M[2]);
+      const int slot = ez % l.EZ;
       const float* gplane = grid + c * Mtot + (size_t)gz * g.M[1] * g.M[0] + gx;
-      const int idx = ez * l.Q + lane;
+      const int idx = slot * l.Q + lane;
       float* dst = c == 0 ? ext + idx : ext + yz_plane_offset(l) + 2 * idx + (c - 1);
       unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
       const unsigned sstep = (c == 0 ? 4u : 8u) * (unsigned)l.P;
