@@ -349,6 +349,13 @@ void launch_spread_tc(const Geometry<float>& g, const KernelConsts<float>& kc, b
 bool spread_mma_eligible(const int tile[3], int MG);
 void launch_spread_mma(const Geometry<float>& g, const KernelConsts<float>& kc, bool torque, const BinBuffers& b,
                        float* grid, cudaStream_t s);
+// SMs of the current device (launch sizing of the pencil kernels).
+inline int device_sm_count() {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
 void launch_gather_f32(const Geometry<float>& g, const KernelConsts<float>& kc, bool torque,
                        const BinBuffers& b, const float* grid, const float* upair, const float* wpair,
                        float* U, float* W, cudaStream_t s, long long* launches);

@@ -24,14 +24,18 @@ __global__ void __launch_bounds__(256) gather_tile_kernel(Geometry<float> g, Ker
                                                           const float* __restrict__ grid,
                                                           const float* __restrict__ upair,
                                                           const float* __restrict__ wpair,
-                                                          float* __restrict__ U, float* __restrict__ W) {
+                                                          float* __restrict__ U, float* __restrict__ W,
+                                                          int segl) {
   extern __shared__ float4 sm4[];
   float* acc = reinterpret_cast<float*>(sm4);
-  // the CTA's z-pencil of tiles (tx, ty, 0 .. ntile_z - 1) of one system, walked in z
+  // the CTA's segment (segl tiles) of a z-pencil of tiles (tx, ty, 0 .. ntile_z - 1) of one system, walked in z
   const int ntx = g.ntile[0], nty = g.ntile[1], ntz = g.ntile[2];
   const int per = ntx * nty;
-  const int sys = blockIdx.x / per;
-  const int pcl = blockIdx.x - sys * per;
+  const int nseg = (ntz + segl - 1) / segl;
+  const int sys = blockIdx.x / (per * nseg);
+  const int rem = blockIdx.x - sys * per * nseg;
+  const int pcl = rem / nseg;
+  const int z0 = (rem - pcl * nseg) * segl, z1 = min(ntz, z0 + segl);
   const int tx = pcl % ntx, ty = pcl / ntx;
   const int tbase = sys * g.tiles_per + pcl;   // tile (tx, ty, 0): tiles are numbered x fastest
   if (g.nsys > 1) grid += (size_t)sys * (size_t)g.grid_stride;
@@ -43,7 +47,7 @@ __global__ void __launch_bounds__(256) gather_tile_kernel(Geometry<float> g, Ker
   pen.oy0 = ty * g.tile[1];
   pen.oz0 = 0;
   int staged = 0;   // pencil planes below this are in the ring (plane P in slot P mod E_Z)
-  for (int tz = 0; tz < ntz; ++tz) {
+  for (int tz = z0; tz < z1; ++tz) {
     const int t = tbase + per * tz;
     const int p0 = tstart[t], p1 = tstart[t + 1];
     if (p0 >= p1) continue;
@@ -249,8 +253,13 @@ static void gather_variant(const Geometry<float>& g, const KernelConsts<float>& 
   auto k = gather_tile_kernel<MGT, GUARD, TORQUE, SAMEW>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int nsys = g.nsys > 1 ? g.nsys : 1;
-  const int blocks = nsys * g.ntile[0] * g.ntile[1];   // one CTA per z-pencil of tiles
-  k<<<blocks, 256, smem, s>>>(g, kc, (const float4*)b.t_pos, b.tile_start, grid, up, wp, U, W);
+  const int pencils = nsys * g.ntile[0] * g.ntile[1];
+  // one CTA per z-pencil of tiles; pencils are split into segments when there are too few of them for
+  // two waves of two CTAs per SM
+  const int nseg = std::min(g.ntile[2], std::max(1, (4 * device_sm_count() + pencils - 1) / pencils));
+  const int segl = (g.ntile[2] + nseg - 1) / nseg;
+  const int blocks = pencils * ((g.ntile[2] + segl - 1) / segl);
+  k<<<blocks, 256, smem, s>>>(g, kc, (const float4*)b.t_pos, b.tile_start, grid, up, wp, U, W, segl);
 }
 
 void launch_gather_f32(const Geometry<float>& g, const KernelConsts<float>& kc, bool torque,

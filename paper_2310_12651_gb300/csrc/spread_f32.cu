@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(rows_threads(MGT), 1) spread_pencil_kernel(Geo
                                                                           const float4* __restrict__ Fv,
                                                                           const float4* __restrict__ Tv,
                                                                           const int* __restrict__ tstart,
-                                                                          float* __restrict__ grid) {
+                                                                          float* __restrict__ grid, int segl) {
   constexpr int NP = row_pairs(MGT);
   constexpr int NK = (NP + 1) / 2;
   constexpr int EXT2 = pencil_pairs(MGT);
@@ -447,10 +447,13 @@ __global__ void __launch_bounds__(rows_threads(MGT), 1) spread_pencil_kernel(Geo
   extern __shared__ float4 sm4[];
   const int ntx = g.ntile[0], nty = g.ntile[1];
   const int per = nty * g.ntile[2];
-  const int sys = blockIdx.x / per;
-  const int pc = blockIdx.x - sys * per;
+  const int nseg = (ntx + segl - 1) / segl;              // segments of segl tiles per pencil
+  const int sys = blockIdx.x / (per * nseg);
+  const int rem = blockIdx.x - sys * per * nseg;
+  const int pc = rem / nseg;
+  const int s0 = (rem - pc * nseg) * segl, s1 = min(ntx, s0 + segl);   // this CTA's tiles of the pencil
   const int t0 = sys * g.tiles_per + ntx * pc;          // tile (0, ty, tz) of the pencil
-  const int p_begin = tstart[t0], p_end = tstart[t0 + ntx];
+  const int p_begin = tstart[t0 + s0], p_end = tstart[t0 + s1];
   if (p_begin >= p_end) return;
   if (g.nsys > 1) grid += (size_t)sys * (size_t)g.grid_stride;
   const int oy0 = (pc % nty) * g.tile[1], oz0 = (pc / nty) * g.tile[2];
@@ -467,7 +470,7 @@ __global__ void __launch_bounds__(rows_threads(MGT), 1) spread_pencil_kernel(Geo
     sy[k] = make_float2(0.f, 0.f);
     sz[k] = make_float2(0.f, 0.f);
   }
-  int cur = 0;   // tile step whose x origin anchors the register row
+  int cur = s0;   // tile step whose x origin anchors the register row
   constexpr int C = pencil_chunk(MGT, MODE);
   // profile tables of one pass (particles [base, base + np)) from its raw rows
   auto build = [&](const PencilTables& tb, const float4* rpos, int np) {
@@ -783,11 +786,16 @@ static void pencil_variant(const Geometry<float>& g, const KernelConsts<float>& 
   const size_t smem = pencil_tables_bytes(MGT, MODE);
   const int threads = (((g.tile[1] + g.MG - 1) * (g.tile[2] + g.MG - 1) + 31) / 32) * 32;
   const int nsys = g.nsys > 1 ? g.nsys : 1;
-  const int blocks = nsys * g.ntile[1] * g.ntile[2];
+  const int pencils = nsys * g.ntile[1] * g.ntile[2];
+  // Long pencils are split into segments when there are too few pencils for two waves of one CTA per SM
+  // (thin slabs, small single systems); a segment flushes its whole register row at its end.
+  const int nseg = std::min(g.ntile[0], std::max(1, (2 * device_sm_count() + pencils - 1) / pencils));
+  const int segl = (g.ntile[0] + nseg - 1) / nseg;
+  const int blocks = pencils * ((g.ntile[0] + segl - 1) / segl);
   auto k = spread_pencil_kernel<MGT, GUARD, MODE>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k<<<blocks, threads, smem, s>>>(g, kc, (const float4*)b.t_pos, (const float4*)b.t_F, (const float4*)b.t_T,
-                                  b.tile_start, grid);
+                                  b.tile_start, grid, segl);
 }
 
 size_t spread_smem_bytes(const int tile[3], int MG) {
