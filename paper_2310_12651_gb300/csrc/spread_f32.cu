@@ -787,9 +787,9 @@ static void pencil_variant(const Geometry<float>& g, const KernelConsts<float>& 
   const int threads = (((g.tile[1] + g.MG - 1) * (g.tile[2] + g.MG - 1) + 31) / 32) * 32;
   const int nsys = g.nsys > 1 ? g.nsys : 1;
   const int pencils = nsys * g.ntile[1] * g.ntile[2];
-  // Long pencils are split into segments when there are too few pencils for two waves of one CTA per SM
+  // Long pencils are split into segments when there are too few pencils for four waves of one CTA per SM
   // (thin slabs, small single systems); a segment flushes its whole register row at its end.
-  const int nseg = std::min(g.ntile[0], std::max(1, (2 * device_sm_count() + pencils - 1) / pencils));
+  const int nseg = std::min(g.ntile[0], std::max(1, (4 * device_sm_count() + pencils - 1) / pencils));
   const int segl = (g.ntile[0] + nseg - 1) / nseg;
   const int blocks = pencils * ((g.ntile[0] + segl - 1) / segl);
   auto k = spread_pencil_kernel<MGT, GUARD, MODE>;
