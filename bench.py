@@ -1169,7 +1169,7 @@ def main():
     ms_per_step = total_ms / args.steps
 
     # ---- the FFT chain alone: grid-part passes (no pair kernel beside it on the side stream)
-    fft_alone = None
+    fft_alone = gather_alone = pair_alone = None
     if batched:
         h.set_timing(True)
         h.read_timing()
@@ -1177,10 +1177,19 @@ def main():
             flush.zero_()
             h.batch_apply(offsets, pos_all, F_all, T_all, U, W, sptr, stages=fcm.STAGE_GRID)
         st_alone = h.read_timing()
-        h.set_timing(False)
         ms_fft, cnt_fft = st_alone["fft_solve"]
         if cnt_fft:
             fft_alone = ms_fft / cnt_fft
+        ms_g, cnt_g = st_alone["gather"]
+        gather_alone = ms_g / cnt_g if cnt_g else None
+        # the pair kernel alone: pair-only passes (inside the full pass it shares the SMs with the FFT chain
+        # and the gather)
+        for k in range(3):
+            flush.zero_()
+            h.batch_apply(offsets, pos_all, F_all, T_all, U, W, sptr, stages=fcm.STAGE_PAIR)
+        ms_p, cnt_p = h.read_timing()["pair"]
+        h.set_timing(False)
+        pair_alone = ms_p / cnt_p if cnt_p else None
 
     # ---- end to end through host buffers: pinned host -> device inputs, the pass, device -> host outputs
     hpos, hF, hT = (t.cpu().pin_memory() for t in (pos_all, F_all, T_all))
@@ -1265,6 +1274,15 @@ def main():
         stages_out["fft_solve"]["GBps"] = fft_bytes / (fft_alone * 1e-3) / 1e9
         stages_out["fft_solve"]["frac_hbm"] = stages_out["fft_solve"]["GBps"] / hbm
         stages_out["fft_solve"]["bytes"] = "72 B per grid point: 6 transforms x 8 B + 24 B for the projection kernel"
+    if gather_alone:
+        stages_out["gather"]["ms_alone"] = gather_alone
+    if pair_alone:
+        stages_out["pair"]["ms_alone"] = pair_alone
+        stages_out["pair"]["TFLOPs_alone"] = flops["pair"] / (pair_alone * 1e-3) / 1e12
+        stages_out["pair"]["frac_alu_alone"] = stages_out["pair"]["TFLOPs_alone"] / alu_peak
+    if avg["pair"]:
+        stages_out["pair"]["TFLOPs"] = flops["pair"] / (avg["pair"] * 1e-3) / 1e12
+        stages_out["pair"]["frac_alu"] = stages_out["pair"]["TFLOPs"] / alu_peak
     for s_ in ("spread", "gather"):
         if avg[s_]:
             stages_out[s_]["TFLOPs"] = flops[s_] / (avg[s_] * 1e-3) / 1e12
