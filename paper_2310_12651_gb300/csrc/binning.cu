@@ -7,6 +7,10 @@
 // start offsets used by the pair correction. The rank of a particle inside its
 // bin is the value its atomic increment returned, so three kernels suffice:
 // key+count, scan, scatter. The scan leaves the counters at zero for the next call.
+// Inside a tile, particles whose window starts in the first half of the tile's x
+// range come first: they count on tile_count[t], the others on tile_count[ntiles + t]
+// and are placed from tile_start[ntiles + 1 + t] (the pencil spread steps half a
+// tile at a time along x).
 #include "fcm_internal.cuh"
 
 namespace fcm {
@@ -30,19 +34,22 @@ __global__ void __launch_bounds__(256) key_count_kernel(Geometry<R> g, int n, co
   if (i >= n) return;
   const int sys = system_of(b, i);
   int bad = 0;
-  int t[3], c[3];
+  int t[3], c[3], xoff = 0;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     R y = wrap_coord(pos[3 * (size_t)i + d], g.L[d], &bad);
     int i0 = pmod(window_start_d(g, d, y), g.M[d]);
     t[d] = i0 / g.tile[d];
+    if (d == 0) xoff = i0 - t[0] * g.tile[0];
     c[d] = cell_coord(y, g.cellw_inv[d], g.mcell[d]);
   }
   if (bad) atomicOr(b.status, kStatusNonFinite);
   unsigned tk = (unsigned)(t[0] + g.ntile[0] * (t[1] + g.ntile[1] * t[2]));
   if (sys) tk += (unsigned)sys * (unsigned)g.tiles_per;
   b.tile_key[i] = tk;
-  b.tile_rank[i] = (unsigned)atomicAdd(&b.tile_count[tk], 1);
+  const unsigned half = (g.tile[0] >= 2 && xoff >= (g.tile[0] >> 1)) ? 1u : 0u;
+  const unsigned rank = (unsigned)atomicAdd(&b.tile_count[tk + (half ? (unsigned)b.ntiles : 0u)], 1);
+  b.tile_rank[i] = rank | (half << 31);
   if (need_cells) {
     unsigned ck = (unsigned)(c[0] + g.mcell[0] * (c[1] + g.mcell[1] * c[2]));
     if (sys) ck += (unsigned)sys * (unsigned)g.cells_per;
@@ -52,15 +59,17 @@ __global__ void __launch_bounds__(256) key_count_kernel(Geometry<R> g, int n, co
 }
 
 // Exclusive scan of one counter array by one block, offset by base; start[nb] = base + total
-// when write_end. Resets counts.
-__device__ void block_scan(int* count, int* start, int nb, int base, bool write_end) {
+// when write_end. Resets counts. With count1 (a second counter per bin, placed after the first's
+// particles), bin k holds count[k] + count1[k] particles and start1[k] = start[k] + count[k].
+__device__ void block_scan(int* count, int* start, int nb, int base, bool write_end, int* count1 = nullptr,
+                           int* start1 = nullptr) {
   __shared__ int warp_sums[32];
   __shared__ int carry;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int chunk = (nb + nthr - 1) / nthr;
   const int lo = min(nb, tid * chunk), hi = min(nb, lo + chunk);
   int local = 0;
-  for (int k = lo; k < hi; ++k) local += count[k];
+  for (int k = lo; k < hi; ++k) local += count[k] + (count1 ? count1[k] : 0);
   // inclusive warp scan of the per-thread sums
   int lane = tid & 31, wid = tid >> 5;
   int v = local;
@@ -85,10 +94,15 @@ __device__ void block_scan(int* count, int* start, int nb, int base, bool write_
   __syncthreads();
   int excl = base + v - local + (wid > 0 ? warp_sums[wid - 1] : 0);
   for (int k = lo; k < hi; ++k) {
-    int cnt = count[k];
+    const int cnt = count[k];
     start[k] = excl;
     excl += cnt;
     count[k] = 0;
+    if (count1) {
+      start1[k] = excl;
+      excl += count1[k];
+      count1[k] = 0;
+    }
   }
   if (tid == 0 && write_end) start[nb] = base + carry;
 }
@@ -103,7 +117,8 @@ __global__ void __launch_bounds__(1024) scan_kernel(BinBuffers b, int need_cells
   const bool last = sys == nsys - 1;
   if (blockIdx.x == 0) {
     const int per = b.ntiles / nsys;
-    block_scan(b.tile_count + (size_t)sys * per, b.tile_start + (size_t)sys * per, per, base, last);
+    block_scan(b.tile_count + (size_t)sys * per, b.tile_start + (size_t)sys * per, per, base, last,
+               b.tile_count + (size_t)b.ntiles + (size_t)sys * per, b.tile_start + (size_t)b.ntiles + 1 + (size_t)sys * per);
   } else if (need_cells) {
     const int per = b.ncells / nsys;
     block_scan(b.cell_count + (size_t)sys * per, b.cell_start + (size_t)sys * per, per, base, last);
@@ -128,7 +143,9 @@ __global__ void __launch_bounds__(256) scatter_kernel(Geometry<R> g, int n, cons
   else   { t.x = R(0); t.y = R(0); t.z = R(0); }
   t.w = R(0);
   // keys and ranks come from key_count_kernel; both bins are in range by construction
-  int dt = b.tile_start[b.tile_key[i]] + (int)b.tile_rank[i];
+  const unsigned rk = b.tile_rank[i];
+  int dt = b.tile_start[(rk >> 31) ? (size_t)b.ntiles + 1 + b.tile_key[i] : (size_t)b.tile_key[i]] +
+           (int)(rk & 0x7fffffffu);
   dt = min(max(dt, 0), n - 1);
   ((Vec4<R>*)b.t_pos)[dt] = p;
   ((Vec4<R>*)b.t_F)[dt] = f;

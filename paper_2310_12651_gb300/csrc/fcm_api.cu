@@ -671,7 +671,7 @@ size_t workspace_estimate(const fcm_params& p, int max_systems) {
   const size_t mtot = (size_t)p.M[0] * p.M[1] * p.M[2];
   const size_t ncplx = (size_t)(p.M[0] / 2 + 1) * p.M[1] * p.M[2];
   const size_t ntiles = (size_t)g.tiles_per * gsys, ncells = (size_t)g.cells_per * gsys;
-  size_t b = 16 * n + 8 * (ntiles + 1) + 8 * (ncells + 1) + 6 * v4 * n + 256 + 4 * (kMaxBatch + 1) + 9 * rsz * n;
+  size_t b = 16 * n + 8 * (2 * ntiles + 1) + 8 * (ncells + 1) + 6 * v4 * n + 256 + 4 * (kMaxBatch + 1) + 9 * rsz * n;
   b += (3 * rsz * mtot + 6 * rsz * ncplx) * gsys + sizeof(float4) * 5 * kPairTableIntervals;
   int dims[3] = {p.M[2], p.M[1], p.M[0]};
   size_t w1 = 0, w2 = 0;
@@ -1172,7 +1172,7 @@ int fcm_create_batch(const fcm_params* p, int max_systems, int device, fcm_handl
   b.ncells = pairs_on ? (int)ncells_d : 1;
   A((void**)&b.tile_key, 4 * n); A((void**)&b.tile_rank, 4 * n);
   A((void**)&b.cell_key, 4 * n); A((void**)&b.cell_rank, 4 * n);
-  A((void**)&b.tile_count, 4 * (size_t)(b.ntiles + 1)); A((void**)&b.tile_start, 4 * (size_t)(b.ntiles + 1));
+  A((void**)&b.tile_count, 4 * (size_t)(2 * b.ntiles + 1)); A((void**)&b.tile_start, 4 * (size_t)(2 * b.ntiles + 1));
   A((void**)&b.cell_count, 4 * (size_t)(b.ncells + 1)); A((void**)&b.cell_start, 4 * (size_t)(b.ncells + 1));
   A(&b.t_pos, v4 * n); A(&b.t_F, v4 * n); A(&b.t_T, v4 * n);
   A(&b.c_pos, v4 * n); A(&b.c_F, v4 * n); A(&b.c_T, v4 * n);
@@ -1201,7 +1201,7 @@ int fcm_create_batch(const fcm_params* p, int max_systems, int device, fcm_handl
     h->ptab.inv_h = (float)(nint / (r_hi - r_lo));
     h->ptab.n = nint;
   }
-  cudaError_t ce = cudaMemset(b.tile_count, 0, 4 * (size_t)(b.ntiles + 1));
+  cudaError_t ce = cudaMemset(b.tile_count, 0, 4 * (size_t)(2 * b.ntiles + 1));
   if (ce == cudaSuccess) ce = cudaMemset(b.cell_count, 0, 4 * (size_t)(b.ncells + 1));
   if (ce == cudaSuccess) ce = cudaMemset(b.status, 0, 256);
   if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);

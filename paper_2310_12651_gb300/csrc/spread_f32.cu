@@ -252,11 +252,13 @@ __global__ void __launch_bounds__(rows_threads(MGT), 1) spread_rows_kernel(Geome
 // x-pencil of binning tiles (all tiles with the same (y, z) tile index of one system; they are
 // contiguous in the tile-sorted order). Every thread owns one (y, z) row of the pencil's extended
 // (y, z) region and keeps a register row of EXT2 point pairs per component, anchored at the current
-// tile's x origin x0 = 8 s. Particles of tile s have window starts in [x0, x0 + 8), so once the walk
-// passes to tile s + 1 the points x0 .. x0 + 7 are complete for this pencil: they are added to the
-// grid (four pairs per component) and the register row shifts by four pairs. The x halo of one tile
-// is thus carried into the next tile in registers instead of being added to the grid, and only the
-// (y, z) halo is flushed with global reductions. A particle's row update is predicated (coefficients
+// half tile's x origin x0 = 4 s. The binning orders each tile's particles by the half of the tile
+// their window starts in, so the particles of half tile s, taken in order, have window starts in
+// [x0, x0 + 4): once the walk passes to half tile s + 1 the points x0 .. x0 + 3 are complete for this
+// pencil, they are added to the grid (two pairs per component) and the register row shifts by two
+// pairs. Walking half tiles keeps the row at M_G / 2 + 2 pairs (a window starts at one of two pairs)
+// instead of M_G / 2 + 4. The x halo is thus carried along the pencil in registers instead of being
+// added to the grid, and only the (y, z) halo is flushed with global reductions. A particle's row update is predicated (coefficients
 // zero outside its window): a warp skips a particle only when none of its rows is in the window, so
 // no lane diverges.
 //
@@ -281,8 +283,9 @@ __host__ __device__ constexpr int pencil_chunk(int MGT, int MODE) {
   return (MODE != kPencilTwoWidths && MGT <= 14) ? 128 : 64;
 }
 
-// Register pairs of a pencil row: window pairs start at pair ox / 2 with ox in [0, 8).
-__host__ __device__ constexpr int pencil_pairs(int MGT) { return row_pairs(MGT) + 3; }
+// Register pairs of a pencil row: the walk steps half a tile (4 points) at a time, so window pairs start at
+// pair ox / 2 with ox in [0, 4) (the binning puts each tile's particles with ox < 4 first).
+__host__ __device__ constexpr int pencil_pairs(int MGT) { return row_pairs(MGT) + 1; }
 
 // Per-particle tables of the pencil kernel (one staged chunk).
 struct PencilTables {
@@ -430,7 +433,7 @@ __device__ __forceinline__ void pencil_flush(int x0, int Mx, bool vec_rows, floa
 template <int EXT2>
 __device__ __forceinline__ void pencil_shift(float2 (&s)[EXT2]) {
 #pragma unroll
-  for (int k = 0; k < EXT2; ++k) s[k] = (k + 4 < EXT2) ? s[k + 4] : make_float2(0.f, 0.f);
+  for (int k = 0; k < EXT2; ++k) s[k] = (k + 2 < EXT2) ? s[k + 2] : make_float2(0.f, 0.f);
 }
 
 template <int MGT, bool GUARD, int MODE>
@@ -470,7 +473,7 @@ __global__ void __launch_bounds__(rows_threads(MGT), 1) spread_pencil_kernel(Geo
     sy[k] = make_float2(0.f, 0.f);
     sz[k] = make_float2(0.f, 0.f);
   }
-  int cur = s0;   // tile step whose x origin anchors the register row
+  int cur = 2 * s0;   // half-tile step whose x origin (4 cur) anchors the register row
   constexpr int C = pencil_chunk(MGT, MODE);
   // profile tables of one pass (particles [base, base + np)) from its raw rows
   auto build = [&](const PencilTables& tb, const float4* rpos, int np) {
@@ -531,11 +534,12 @@ __global__ void __launch_bounds__(rows_threads(MGT), 1) spread_pencil_kernel(Geo
       const int3 i0 = window_starts(g, y);
       const int wx = wrap_once(i0.x, g.M[0]);
       const int step = min(max(wx >> 3, 0), ntx - 1);
+      const int ox = min(max(wx - 8 * step, 0), 7);   // the binning's half of the tile: ox >= 4
       int4 off;
-      off.x = min(max(wx - 8 * step, 0), 7);
+      off.x = ox & 3;
       off.y = min(max(wrap_once(i0.y, g.M[1]) - oy0, 0), g.tile[1] - 1);
       off.z = min(max(wrap_once(i0.z, g.M[2]) - oz0, 0), g.tile[2] - 1);
-      off.w = step;
+      off.w = 2 * step + (ox >> 2);
       tb.po[q] = off;
       const float4 f = rF[q];
       const float4 t = TORQUE ? rT[q] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -564,15 +568,15 @@ __global__ void __launch_bounds__(rows_threads(MGT), 1) spread_pencil_kernel(Geo
     const PencilTables tb = pencil_tables<MGT, MODE>(sm4, pass & 1);
     for (int q = 0; q < np; ++q) {
       const int4 off = tb.po[q];
-      // the walk reaches the particle's tile: complete points of the passed tiles go to the grid
+      // the walk reaches the particle's half tile: complete points of the passed half tiles go to the grid
       while (cur < off.w) {
         if (has_row) {
           const size_t Mtot = (size_t)g.M[0] * g.M[1] * g.M[2];
           float* r0 = grid + ((size_t)wrap_index(oz0 + ez, g.M[2]) * g.M[1] + wrap_index(oy0 + ey, g.M[1])) * g.M[0];
           const bool vec_rows = (g.M[0] & 3) == 0;
-          pencil_flush<EXT2>(8 * cur, g.M[0], vec_rows, r0, sx, 0, 4);
-          pencil_flush<EXT2>(8 * cur, g.M[0], vec_rows, r0 + Mtot, sy, 0, 4);
-          pencil_flush<EXT2>(8 * cur, g.M[0], vec_rows, r0 + 2 * Mtot, sz, 0, 4);
+          pencil_flush<EXT2>(4 * cur, g.M[0], vec_rows, r0, sx, 0, 2);
+          pencil_flush<EXT2>(4 * cur, g.M[0], vec_rows, r0 + Mtot, sy, 0, 2);
+          pencil_flush<EXT2>(4 * cur, g.M[0], vec_rows, r0 + 2 * Mtot, sz, 0, 2);
         }
         pencil_shift<EXT2>(sx);
         pencil_shift<EXT2>(sy);
@@ -628,7 +632,7 @@ __global__ void __launch_bounds__(rows_threads(MGT), 1) spread_pencil_kernel(Geo
                                     c[8], c[9], c[10]);                                                         \
     break;
       switch (off.x >> 1) {
-        FCM_PENCIL_CASE(0) FCM_PENCIL_CASE(1) FCM_PENCIL_CASE(2) FCM_PENCIL_CASE(3)
+        FCM_PENCIL_CASE(0) FCM_PENCIL_CASE(1)
         default: break;
       }
 #undef FCM_PENCIL_CASE
@@ -643,9 +647,9 @@ __global__ void __launch_bounds__(rows_threads(MGT), 1) spread_pencil_kernel(Geo
     const size_t Mtot = (size_t)g.M[0] * g.M[1] * g.M[2];
     float* r0 = grid + ((size_t)wrap_index(oz0 + ez, g.M[2]) * g.M[1] + wrap_index(oy0 + ey, g.M[1])) * g.M[0];
     const bool vec_rows = (g.M[0] & 3) == 0;
-    pencil_flush<EXT2>(8 * cur, g.M[0], vec_rows, r0, sx, 0, EXT2);
-    pencil_flush<EXT2>(8 * cur, g.M[0], vec_rows, r0 + Mtot, sy, 0, EXT2);
-    pencil_flush<EXT2>(8 * cur, g.M[0], vec_rows, r0 + 2 * Mtot, sz, 0, EXT2);
+    pencil_flush<EXT2>(4 * cur, g.M[0], vec_rows, r0, sx, 0, EXT2);
+    pencil_flush<EXT2>(4 * cur, g.M[0], vec_rows, r0 + Mtot, sy, 0, EXT2);
+    pencil_flush<EXT2>(4 * cur, g.M[0], vec_rows, r0 + 2 * Mtot, sz, 0, EXT2);
   }
 }
 
