@@ -51,7 +51,7 @@ WORKLOADS = {
 }
 # dram__bytes_read.sum + dram__bytes_write.sum per system of a launch (cold caches), from one ncu capture of
 # the current kernels; a launch over B systems moves B times this. None once a kernel changes after the capture.
-TRAFFIC_BYTES = {"c2": {"spread": 29.37e6, "gather": 26.49e6, "pair": 4.75e6}}
+TRAFFIC_BYTES = {"c2": {"spread": 29.16e6, "gather": 26.49e6, "pair": 4.75e6}}
 # Algorithmic work per unit for the roofline (the hot-path scope table's figures): flops per (particle,
 # window point) of the spread and of the gather, and per ordered pair within r_c of the pair correction;
 # forces + torques and forces only.
